@@ -1,0 +1,172 @@
+/*
+ * agipc.h - C ABI of the GB300 in-solve algebraic coarsening step.
+ *
+ * One Newton iteration of the adaptive solver of arxiv 2605.04773 (Algorithm 1:
+ * the mapping update, the mapping of H and grad E to the coarse level, the
+ * coarse solve, and the prolongation of Sec. 4.3) as four calls:
+ *
+ *   agipc_aggregate        tags -> super-node labels            (Sec. 4.1; supplement Sec. 1)
+ *   agipc_assemble_coarse  labels, H, g -> H_c = U H U^T, g_c = U g, block-Jacobi (Sec. 4.1; supplement Sec. 2)
+ *   agipc_pcg              H_c y = -g_c by block-Jacobi PCG      (Algorithm 1; Sec. 5, Preconditioners)
+ *   agipc_prolongate       dx = U^T y                            (Sec. 4.3)
+ *
+ * Conventions for every call:
+ *   - All array arguments are DEVICE pointers owned by the caller; the
+ *     library never frees them.  Scratch memory belongs to the context and is
+ *     allocated once by agipc_create.
+ *   - Every call is asynchronous: it checks its host-side arguments, enqueues
+ *     kernels on the context's CUDA stream and returns.  Errors that only the
+ *     GPU can see (non-finite values, capacity overflow, PCG not converged,
+ *     a bounded device wait that ran out) are OR-ed into a device status word;
+ *     agipc_status() synchronizes the stream, returns the first of them as a
+ *     status code and clears the word.
+ *   - Sizes that only the GPU knows (n_c, nnz_c, PCG iterations) stay in
+ *     caller-owned device scalars, so a whole step can be captured in a CUDA
+ *     graph.  Nothing here synchronizes with the host except agipc_status and
+ *     agipc_destroy.
+ *   - 3x3 blocks are 9 contiguous FP64 values in row-major order; vectors of
+ *     nodes are [n][3] FP64.  Index arrays are int32.
+ *   - Return value: AGIPC_OK or a negative AGIPC_ERR_* code.
+ */
+#ifndef AGIPC_H
+#define AGIPC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    AGIPC_OK = 0,
+    AGIPC_ERR_INVALID_ARG = -1,   /* host-checked argument error; nothing was enqueued */
+    AGIPC_ERR_CUDA = -2,          /* a CUDA runtime call failed */
+    AGIPC_ERR_CAPACITY = -3,      /* an output would exceed its caller-given capacity */
+    AGIPC_ERR_NONFINITE = -4,     /* NaN/Inf met, or a singular diagonal block */
+    AGIPC_ERR_NOT_CONVERGED = -5, /* PCG hit max_iter; x holds the last iterate */
+    AGIPC_ERR_TIMEOUT = -6,       /* a bounded device-side wait gave up */
+    AGIPC_ERR_BAD_INDEX = -7      /* an index array held a value out of range */
+};
+
+typedef struct agipc_ctx agipc_ctx;
+
+/*
+ * Create a context bound to the current CUDA device and to `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  Scratch memory is
+ * sized for the largest problem the context will see:
+ *   max_fine_nodes    n of any fine system
+ *   max_edges         mesh edges passed to agipc_aggregate
+ *   max_fine_nnzb     3x3 blocks of any fine upper-triangular BSR matrix
+ *   max_pairs         barrier stencils passed to agipc_assemble_coarse
+ * The largest matrix agipc_pcg will accept then has 2*max_fine_nnzb +
+ * 16*max_pairs blocks and max_fine_nodes rows.  Returns INVALID_ARG on a
+ * negative size and CUDA when device memory cannot be had.
+ */
+int agipc_create(agipc_ctx **ctx, void *cuda_stream, int32_t max_fine_nodes, int64_t max_edges,
+                 int64_t max_fine_nnzb, int64_t max_pairs);
+
+/* Synchronize the context's stream and release its scratch memory. */
+int agipc_destroy(agipc_ctx *ctx);
+
+/* Rebind the context to another stream (e.g. the caller's current stream). */
+int agipc_set_stream(agipc_ctx *ctx, void *cuda_stream);
+
+/*
+ * Super-node labels (Sec. 4.1: nodes are coalesced only across paths of
+ * collapsible edges; supplement Sec. 1, Algorithms 1-2 and the worked
+ * examples of Sec. 1.2-1.3).
+ *   n_fine            number of fine nodes
+ *   n_edges           number of mesh edges
+ *   edges   [E][2]    int32 endpoints, any order, 0 <= u, v < n_fine
+ *   tags    [E]       uint8, nonzero = collapsible (tau_e = 1), 0 = protected
+ *   labels  [n_fine]  out: int32 coarse index of every fine node
+ *   n_coarse_dev      out: device int32, the number of super-nodes n_c
+ * Labels are the connected components of the collapsible-edge graph, ranked
+ * by each component's smallest fine index (the supplement's ordering: first
+ * set bit of the group hash, then a prefix sum over groups), so they are
+ * dense in [0, n_c) and identical whatever the GPU's scheduling.
+ * Out-of-range endpoints set AGIPC_ERR_BAD_INDEX in the status word.
+ */
+int agipc_aggregate(agipc_ctx *ctx, int32_t n_fine, int64_t n_edges, const int32_t *edges, const uint8_t *tags,
+                    int32_t *labels, int32_t *n_coarse_dev);
+
+/*
+ * Coarse system (Sec. 4.1: g_c = sum of the children's g_f; each fine 3x3
+ * block (i, j) is summed into (map(i), map(j)), i.e. H_c = U H U^T;
+ * supplement Sec. 2 for the reduction; contact Hessians join the fine
+ * system before coarsening, Sec. 4.3).
+ *   n_fine, labels, n_coarse_dev      as produced by agipc_aggregate
+ *   fine_row_ptr [n_fine+1], fine_col [fine_nnzb], fine_val [fine_nnzb][9]
+ *                   the fine Hessian's diagonal and upper triangle (col >= row)
+ *                   as BSR; each diagonal block must be symmetric
+ *   n_pairs, pair_idx [P][4], pair_blk [P][10][9]
+ *                   barrier stencils: 4 vertices and the 10 upper 3x3 blocks in
+ *                   the local order (0,0),(0,1),(0,2),(0,3),(1,1),(1,2),(1,3),
+ *                   (2,2),(2,3),(3,3); a block (s,t), s<t, also stands for its
+ *                   transpose at (t,s)
+ *   g [n_fine][3]   fine gradient
+ *   coarse_row_ptr [n_fine+1]   out: full-storage BSR of H_c (both triangles),
+ *   coarse_col [cap], coarse_val [cap][9]   columns ascending in each row;
+ *                   row_ptr entries past n_c repeat nnz_c
+ *   coarse_cap_nnzb capacity of coarse_col/coarse_val; 2*fine_nnzb + 16*P
+ *                   always suffices
+ *   coarse_nnzb_dev out: device int32, nnz_c
+ *   g_c [n_fine][3] out: coarse gradient (first n_c rows written)
+ *   dinv [n_fine][9] out: inverses of the diagonal blocks of H_c (block-Jacobi)
+ * With labels = 0..n-1 this is the fine system itself in full storage (the
+ * no-coarsening arm).  Overflowing coarse_cap_nnzb sets AGIPC_ERR_CAPACITY
+ * and leaves the outputs incomplete; a singular or non-finite diagonal block
+ * sets AGIPC_ERR_NONFINITE.
+ */
+int agipc_assemble_coarse(agipc_ctx *ctx, int32_t n_fine, const int32_t *labels, const int32_t *n_coarse_dev,
+                          const int32_t *fine_row_ptr, const int32_t *fine_col, const double *fine_val,
+                          int64_t fine_nnzb, int64_t n_pairs, const int32_t *pair_idx, const double *pair_blk,
+                          const double *g, int32_t *coarse_row_ptr, int32_t *coarse_col, double *coarse_val,
+                          int64_t coarse_cap_nnzb, int32_t *coarse_nnzb_dev, double *g_c, double *dinv);
+
+/* PCG options.  rhs_sign multiplies b (use -1 to solve A y = -g_c from g_c). */
+typedef struct {
+    double tol;          /* stop when ||b - A x||_2 <= tol * ||b||_2 (recurrence residual) */
+    int32_t max_iter;    /* iteration cap; reaching it sets AGIPC_ERR_NOT_CONVERGED */
+    int32_t rhs_sign;    /* +1 or -1 */
+} agipc_pcg_options;
+
+/*
+ * Block-Jacobi preconditioned conjugate gradients, x0 = 0 (Algorithm 1,
+ * d_c = -H_c^-1 g_c; Sec. 5 uses a relative residual-norm stop and Sec. 5.1
+ * the 3x3 block-Jacobi diagonal preconditioner).
+ *   max_rows        host bound on the number of rows (launch sizing)
+ *   n_rows_dev      device int32: the actual number of rows n <= max_rows
+ *   row_ptr [n+1], col, val [..][9]   full-storage SPD BSR matrix
+ *   dinv [n][9]     inverse diagonal blocks
+ *   b [n][3]        right-hand side (scaled by opt->rhs_sign)
+ *   x [n][3]        out: solution
+ *   iters_dev       out: device int32, iterations performed
+ *   relres_dev      out: device double, ||r||_2/||b||_2 at exit
+ * The whole solve runs in one persistent kernel with device-side
+ * convergence, so the host never waits inside the loop.  The iteration is
+ * the Chronopoulos-Gear form of PCG (one fused reduction per iteration);
+ * mathematically it is the same method as the textbook recurrence.
+ */
+int agipc_pcg(agipc_ctx *ctx, int32_t max_rows, const int32_t *n_rows_dev, const int32_t *row_ptr,
+              const int32_t *col, const double *val, const double *dinv, const double *b, double *x,
+              const agipc_pcg_options *opt, int32_t *iters_dev, double *relres_dev);
+
+/*
+ * Prolongation d_f = U^T d_c (Sec. 4.3): dx[f] = y[labels[f]].
+ *   n_fine, labels [n_fine], y [n_c][3]  ->  dx [n_fine][3]
+ */
+int agipc_prolongate(agipc_ctx *ctx, int32_t n_fine, const int32_t *labels, const double *y, double *dx);
+
+/* Synchronize the context's stream; return (and clear) the first device-side
+ * error recorded since the last call, or AGIPC_OK. */
+int agipc_status(agipc_ctx *ctx);
+
+/* Static, human-readable name of a status code. */
+const char *agipc_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AGIPC_H */

@@ -1,0 +1,264 @@
+"""Thin Python binding of the C ABI in include/agipc.h.
+
+Argument marshalling only: every function passes torch CUDA tensors' device
+pointers and the context's stream to libagipc.so, and every step of the
+coarsened solve runs in the library's CUDA kernels.  There is no CPU
+fallback: loading fails loudly when the library is missing or when no CUDA
+device is present.
+
+The function names mirror the C entry points (agipc_aggregate,
+agipc_assemble_coarse, agipc_pcg, agipc_prolongate).  DeviceScene,
+CoarsenedStep and FineStep only allocate output tensors and call those four
+entry points in order.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_CUDA = -2
+ERR_CAPACITY = -3
+ERR_NONFINITE = -4
+ERR_NOT_CONVERGED = -5
+ERR_TIMEOUT = -6
+ERR_BAD_INDEX = -7
+
+_lib = None
+
+
+class AgipcError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__("%s failed: %s (%d)" % (what, status_string(code), code))
+        self.code = code
+
+
+class _PcgOptions(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("rhs_sign", ctypes.c_int32)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libagipc.so (built by build.build()).  Raises if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError("libagipc.so is not built (%s); run paper_2605_04773_gb300.build.build()" % path)
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    i32, i64 = ctypes.c_int32, ctypes.c_int64
+    lib.agipc_create.argtypes = [ctypes.POINTER(P), P, i32, i64, i64, i64]
+    lib.agipc_destroy.argtypes = [P]
+    lib.agipc_set_stream.argtypes = [P, P]
+    lib.agipc_aggregate.argtypes = [P, i32, i64, P, P, P, P]
+    lib.agipc_assemble_coarse.argtypes = [P, i32, P, P, P, P, P, i64, i64, P, P, P, P, P, P, i64, P, P, P]
+    lib.agipc_pcg.argtypes = [P, i32, P, P, P, P, P, P, P, ctypes.POINTER(_PcgOptions), P, P]
+    lib.agipc_prolongate.argtypes = [P, i32, P, P, P]
+    lib.agipc_status.argtypes = [P]
+    lib.agipc_status_string.argtypes = [ctypes.c_int]
+    lib.agipc_status_string.restype = ctypes.c_char_p
+    for name in ("agipc_create", "agipc_destroy", "agipc_set_stream", "agipc_aggregate", "agipc_assemble_coarse",
+                 "agipc_pcg", "agipc_prolongate", "agipc_status"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def status_string(code: int) -> str:
+    return load().agipc_status_string(code).decode()
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise AgipcError(rc, what)
+
+
+class Context:
+    """agipc_create / agipc_destroy.  Bound to torch's current CUDA stream
+    unless another stream is given."""
+
+    def __init__(self, max_fine_nodes: int, max_edges: int, max_fine_nnzb: int, max_pairs: int, stream=None):
+        lib = load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("the coarsening library needs a CUDA device")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        _check(lib.agipc_create(ctypes.byref(h), ctypes.c_void_p(self.stream.cuda_stream), int(max_fine_nodes),
+                                int(max_edges), int(max_fine_nnzb), int(max_pairs)), "agipc_create")
+        self.handle = h
+        self.max_fine_nodes = int(max_fine_nodes)
+
+    def set_stream(self, stream):
+        self.stream = stream
+        _check(load().agipc_set_stream(self.handle, ctypes.c_void_p(stream.cuda_stream)), "agipc_set_stream")
+
+    def status(self) -> int:
+        """Synchronize and return (and clear) the device-side status."""
+        return int(load().agipc_status(self.handle))
+
+    def check(self, allow=(OK,)):
+        rc = self.status()
+        if rc not in allow:
+            raise AgipcError(rc, "device status")
+        return rc
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().agipc_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def agipc_aggregate(ctx: Context, n_fine: int, edges, tags, labels, n_coarse_dev):
+    _check(load().agipc_aggregate(ctx.handle, int(n_fine), int(edges.shape[0]), _ptr(edges), _ptr(tags), _ptr(labels),
+                                  _ptr(n_coarse_dev)), "agipc_aggregate")
+
+
+def agipc_assemble_coarse(ctx: Context, n_fine: int, labels, n_coarse_dev, fine_row_ptr, fine_col, fine_val,
+                          pair_idx, pair_blk, g, coarse_row_ptr, coarse_col, coarse_val, coarse_nnzb_dev, g_c, dinv):
+    _check(load().agipc_assemble_coarse(
+        ctx.handle, int(n_fine), _ptr(labels), _ptr(n_coarse_dev), _ptr(fine_row_ptr), _ptr(fine_col), _ptr(fine_val),
+        int(fine_col.shape[0]), int(pair_idx.shape[0]), _ptr(pair_idx), _ptr(pair_blk), _ptr(g), _ptr(coarse_row_ptr),
+        _ptr(coarse_col), _ptr(coarse_val), int(coarse_col.shape[0]), _ptr(coarse_nnzb_dev), _ptr(g_c), _ptr(dinv)),
+        "agipc_assemble_coarse")
+
+
+def agipc_pcg(ctx: Context, max_rows: int, n_rows_dev, row_ptr, col, val, dinv, b, x, tol: float, max_iter: int,
+              rhs_sign: int, iters_dev, relres_dev):
+    opt = _PcgOptions(float(tol), int(max_iter), int(rhs_sign))
+    _check(load().agipc_pcg(ctx.handle, int(max_rows), _ptr(n_rows_dev), _ptr(row_ptr), _ptr(col), _ptr(val),
+                            _ptr(dinv), _ptr(b), _ptr(x), ctypes.byref(opt), _ptr(iters_dev), _ptr(relres_dev)),
+           "agipc_pcg")
+
+
+def agipc_prolongate(ctx: Context, n_fine: int, labels, y, dx):
+    _check(load().agipc_prolongate(ctx.handle, int(n_fine), _ptr(labels), _ptr(y), _ptr(dx)), "agipc_prolongate")
+
+
+# ---------------------------------------------------------------------------
+# Allocation helpers (marshalling only)
+# ---------------------------------------------------------------------------
+
+
+class DeviceScene:
+    """A scene's solve inputs as contiguous device tensors."""
+
+    def __init__(self, sc, device="cuda"):
+        t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(device=device, dtype=dt)  # noqa: E731
+        self.n = sc.n
+        self.edges = t(sc.edges, torch.int32)
+        self.tags = t(sc.tags, torch.uint8)
+        self.row_ptr = t(sc.row_ptr, torch.int32)
+        self.col = t(sc.col, torch.int32)
+        self.val = t(sc.val.reshape(-1, 9), torch.float64)
+        self.pair_idx = t(sc.pair_idx.reshape(-1, 4), torch.int32)
+        self.pair_blk = t(sc.pair_blk.reshape(-1, 90), torch.float64)
+        self.g = t(sc.g.reshape(-1, 3), torch.float64)
+
+    @property
+    def capacity(self) -> int:
+        return 2 * int(self.col.shape[0]) + 16 * int(self.pair_idx.shape[0])
+
+    def context(self) -> Context:
+        return Context(self.n, self.edges.shape[0], self.col.shape[0], self.pair_idx.shape[0])
+
+
+class CoarsenedStep:
+    """Output buffers of one coarsened Newton-step solve and the four calls
+    that fill them: aggregate -> assemble_coarse -> pcg -> prolongate."""
+
+    def __init__(self, ctx: Context, ds: DeviceScene, tol: float, max_iter: int = 100000):
+        dev = ds.g.device
+        n, cap = ds.n, ds.capacity
+        i32 = dict(device=dev, dtype=torch.int32)
+        f64 = dict(device=dev, dtype=torch.float64)
+        self.ctx, self.ds, self.tol, self.max_iter = ctx, ds, tol, max_iter
+        self.labels = torch.empty(n, **i32)
+        self.n_c = torch.zeros(1, **i32)
+        self.row_ptr = torch.empty(n + 1, **i32)
+        self.col = torch.empty(cap, **i32)
+        self.val = torch.empty(cap, 9, **f64)
+        self.nnz = torch.zeros(1, **i32)
+        self.g_c = torch.empty(n, 3, **f64)
+        self.dinv = torch.empty(n, 9, **f64)
+        self.y = torch.empty(n, 3, **f64)
+        self.dx = torch.empty(n, 3, **f64)
+        self.iters = torch.zeros(1, **i32)
+        self.relres = torch.zeros(1, **f64)
+
+    def aggregate(self, tags=None):
+        ds = self.ds
+        agipc_aggregate(self.ctx, ds.n, ds.edges, ds.tags if tags is None else tags, self.labels, self.n_c)
+
+    def assemble(self):
+        ds = self.ds
+        agipc_assemble_coarse(self.ctx, ds.n, self.labels, self.n_c, ds.row_ptr, ds.col, ds.val, ds.pair_idx,
+                              ds.pair_blk, ds.g, self.row_ptr, self.col, self.val, self.nnz, self.g_c, self.dinv)
+
+    def solve(self):
+        agipc_pcg(self.ctx, self.ds.n, self.n_c, self.row_ptr, self.col, self.val, self.dinv, self.g_c, self.y,
+                  self.tol, self.max_iter, -1, self.iters, self.relres)
+
+    def prolongate(self):
+        agipc_prolongate(self.ctx, self.ds.n, self.labels, self.y, self.dx)
+
+    def run(self, tags=None):
+        self.aggregate(tags)
+        self.assemble()
+        self.solve()
+        self.prolongate()
+
+    def host(self):
+        """Copy the results to host numpy arrays (synchronizes)."""
+        nc = int(self.n_c.item())
+        nnz = int(self.nnz.item())
+        return dict(labels=self.labels.cpu().numpy(), n_c=nc, row_ptr=self.row_ptr[:nc + 1].cpu().numpy(),
+                    col=self.col[:nnz].cpu().numpy(), val=self.val[:nnz].cpu().numpy().reshape(-1, 3, 3),
+                    g_c=self.g_c[:nc].cpu().numpy(), dinv=self.dinv[:nc].cpu().numpy().reshape(-1, 3, 3),
+                    y=self.y[:nc].cpu().numpy(), dx=self.dx.cpu().numpy(), iters=int(self.iters.item()),
+                    relres=float(self.relres.item()))
+
+
+class FineStep:
+    """The no-coarsening arm: identity labels (the fine system in full
+    storage, contacts merged) and PCG on the fine matrix."""
+
+    def __init__(self, ctx: Context, ds: DeviceScene, tol: float, max_iter: int = 100000):
+        self.inner = CoarsenedStep(ctx, ds, tol, max_iter)
+        self.inner.labels.copy_(torch.arange(ds.n, dtype=torch.int32, device=ds.g.device))
+        self.inner.n_c.fill_(ds.n)
+
+    def run(self):
+        self.inner.assemble()
+        self.inner.solve()
+
+    def host(self):
+        return self.inner.host()

@@ -1,0 +1,259 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Labels and the coarse sparsity structure are integer work and must match
+bit for bit.  Coarse blocks and the coarse gradient are FP64 sums whose
+order differs from the oracle's: each entry must agree within 1e-12 times the
+sum of the magnitudes of its contributions (the oracle applied to |H|), and
+the whole matrix within 1e-12 in the Frobenius norm.  A PCG solution is
+judged by its true FP64 residual with the oracle's H_c and g_c, which must be
+within the requested tolerance (5 % slack for the recurrence-vs-true
+residual gap).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2605_04773_gb300 import agipc, scenes
+
+pytestmark = pytest.mark.gpu
+
+VAL_RTOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_04773_gb300 import build
+    build.build()
+    agipc.load()
+
+
+@pytest.fixture(scope="module")
+def domino_full():
+    return scenes.domino_grid(seed=1002)
+
+
+def _run(sc, tags=None, tol=1e-8, max_iter=100000):
+    ds = agipc.DeviceScene(sc)
+    ctx = ds.context()
+    step = agipc.CoarsenedStep(ctx, ds, tol=tol, max_iter=max_iter)
+    if tags is not None:
+        step.aggregate(torch.from_numpy(np.ascontiguousarray(tags, np.uint8)).cuda())
+        step.assemble()
+        step.solve()
+        step.prolongate()
+    else:
+        step.run()
+    rc = ctx.status()
+    out = step.host()
+    ctx.close()
+    return rc, out
+
+
+def _check_coarse(sc, got, tags):
+    lab, nc = oracle.labels(sc.n, sc.edges, tags)
+    assert got["n_c"] == nc
+    assert np.array_equal(got["labels"], lab)
+    crp, cci, cval = oracle.galerkin(lab, nc, sc.row_ptr, sc.col, sc.val, sc.pair_idx, sc.pair_blk)
+    assert np.array_equal(got["row_ptr"], crp)
+    assert np.array_equal(got["col"], cci)
+    _, _, mag = oracle.galerkin(lab, nc, sc.row_ptr, sc.col, np.abs(sc.val), sc.pair_idx, np.abs(sc.pair_blk))
+    err = np.abs(got["val"] - cval)
+    assert np.all(err <= VAL_RTOL * mag + 1e-300), err.max()
+    assert np.linalg.norm(got["val"] - cval) <= VAL_RTOL * np.linalg.norm(cval)
+    # the GPU output mirrors its upper triangle: exactly symmetric
+    for a in range(0, nc, max(1, nc // 64)):
+        for k in range(crp[a], crp[a + 1]):
+            b = cci[k]
+            q = crp[b] + np.searchsorted(cci[crp[b]:crp[b + 1]], a)
+            assert np.array_equal(got["val"][k], got["val"][q].T)
+    gc = oracle.coarse_gradient(lab, nc, sc.g)
+    gmag = oracle.coarse_gradient(lab, nc, np.abs(sc.g))
+    assert np.all(np.abs(got["g_c"] - gc) <= VAL_RTOL * gmag + 1e-300)
+    dinv = oracle.block_jacobi(crp, cci, cval)
+    assert np.abs(got["dinv"] - dinv).max() <= 1e-10 * np.abs(dinv).max()
+    return crp, cci, cval, gc
+
+
+def _check_solve(got, crp, cci, cval, gc, tol):
+    res = oracle.spmv(crp, cci, cval, got["y"]) + gc
+    rel = np.linalg.norm(res) / np.linalg.norm(gc)
+    assert rel <= 1.05 * tol, rel
+    assert got["relres"] <= tol
+    assert np.array_equal(got["dx"], got["y"][got["labels"]])
+    return rel
+
+
+# ------------------------------------------------------------------ labels
+
+
+@pytest.mark.parametrize("pattern", ["scene", "none", "all", "random30", "random95"])
+def test_labels_bit_exact_unit_cube(pattern):
+    sc = scenes.unit_cube(seed=1001)
+    rng = np.random.default_rng(21)
+    tags = {"scene": sc.tags, "none": np.zeros(sc.n_edges, np.uint8), "all": np.ones(sc.n_edges, np.uint8),
+            "random30": (rng.random(sc.n_edges) < 0.3).astype(np.uint8),
+            "random95": (rng.random(sc.n_edges) < 0.95).astype(np.uint8)}[pattern]
+    rc, got = _run(sc, tags)
+    assert rc == agipc.OK
+    _check_coarse(sc, got, tags)
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1), (2, 3, 1), (3, 3, 3), (5, 1, 2), (7, 6, 5)])
+def test_ragged_boxes_full_path(dims):
+    """Node counts that are not multiples of the 32-node group, tiny systems."""
+    sc = scenes.tiny_box(seed=300 + sum(dims), nx=dims[0], ny=dims[1], nz=dims[2], n_pairs=3, frac=0.6)
+    rc, got = _run(sc, tol=1e-10)
+    assert rc == agipc.OK
+    crp, cci, cval, gc = _check_coarse(sc, got, sc.tags)
+    _check_solve(got, crp, cci, cval, gc, 1e-10)
+
+
+def test_labels_random_graph_any_edge_order():
+    """Edges in random order and orientation, self-loops and duplicates."""
+    rng = np.random.default_rng(5)
+    n = 5000
+    e = rng.integers(0, n, size=(12000, 2)).astype(np.int32)
+    e = np.concatenate([e, e[:100], np.stack([np.arange(50), np.arange(50)], 1).astype(np.int32)])
+    tags = (rng.random(e.shape[0]) < 0.5).astype(np.uint8)
+    ctx = agipc.Context(n, e.shape[0], 1, 0)
+    labels = torch.empty(n, dtype=torch.int32, device="cuda")
+    nc = torch.zeros(1, dtype=torch.int32, device="cuda")
+    agipc.agipc_aggregate(ctx, n, torch.from_numpy(e).cuda(), torch.from_numpy(tags).cuda(), labels, nc)
+    assert ctx.status() == agipc.OK
+    ref, rnc = oracle.labels(n, e, tags)
+    assert int(nc.item()) == rnc and np.array_equal(labels.cpu().numpy(), ref)
+    # repeat: bitwise identical whatever the scheduling
+    labels2 = torch.empty_like(labels)
+    agipc.agipc_aggregate(ctx, n, torch.from_numpy(e).cuda(), torch.from_numpy(tags).cuda(), labels2, nc)
+    assert torch.equal(labels, labels2)
+    ctx.close()
+
+
+def test_labels_no_edges():
+    ctx = agipc.Context(100, 1, 1, 0)
+    labels = torch.empty(100, dtype=torch.int32, device="cuda")
+    nc = torch.zeros(1, dtype=torch.int32, device="cuda")
+    e = torch.zeros(0, 2, dtype=torch.int32, device="cuda")
+    t = torch.zeros(0, dtype=torch.uint8, device="cuda")
+    agipc.agipc_aggregate(ctx, 100, e, t, labels, nc)
+    assert ctx.status() == agipc.OK
+    assert int(nc.item()) == 100 and torch.equal(labels.cpu(), torch.arange(100, dtype=torch.int32))
+    ctx.close()
+
+
+# ------------------------------------------------------------------ full path
+
+
+def test_unit_cube_full_path_parity():
+    sc = scenes.unit_cube(seed=1001)
+    rc, got = _run(sc, tol=1e-8)
+    assert rc == agipc.OK
+    crp, cci, cval, gc = _check_coarse(sc, got, sc.tags)
+    _check_solve(got, crp, cci, cval, gc, 1e-8)
+    ref = oracle.coarsened_step(sc, tol=1e-8)
+    assert abs(got["iters"] - ref["iters"]) <= 2
+    assert np.linalg.norm(got["dx"] - ref["dx"]) <= 1e-6 * np.linalg.norm(ref["dx"])
+
+
+def test_single_supernode_and_all_protected():
+    sc = scenes.unit_cube(seed=1003)
+    rc, got = _run(sc, np.ones(sc.n_edges, np.uint8), tol=1e-12)
+    assert rc == agipc.OK and got["n_c"] == 1
+    crp, cci, cval, gc = _check_coarse(sc, got, np.ones(sc.n_edges, np.uint8))
+    assert np.allclose(got["y"][0], -np.linalg.solve(cval[0], gc[0]), rtol=1e-10, atol=0)
+    rc, got = _run(sc, np.zeros(sc.n_edges, np.uint8), tol=1e-8)
+    assert rc == agipc.OK and got["n_c"] == sc.n
+    crp, cci, cval, gc = _check_coarse(sc, got, np.zeros(sc.n_edges, np.uint8))
+    _check_solve(got, crp, cci, cval, gc, 1e-8)
+
+
+def test_domino_small_multibody():
+    sc = scenes.domino_grid(seed=77, gx=2, gy=2, dims=(3, 5, 8), n_pairs=2000)
+    rc, got = _run(sc, tol=1e-8)
+    assert rc == agipc.OK
+    crp, cci, cval, gc = _check_coarse(sc, got, sc.tags)
+    _check_solve(got, crp, cci, cval, gc, 1e-8)
+
+
+def test_domino_full_size_parity(domino_full):
+    """The 64-box, 145,600-vertex, 200k-stencil workload in the bench's launch
+    configuration: labels and structure bit-exact, blocks to 1e-12, solve to
+    1e-6 (true residual)."""
+    sc = domino_full
+    rc, got = _run(sc, tol=1e-6)
+    assert rc == agipc.OK
+    crp, cci, cval, gc = _check_coarse(sc, got, sc.tags)
+    _check_solve(got, crp, cci, cval, gc, 1e-6)
+
+
+def test_fine_arm_full_size(domino_full):
+    """Identity labels: the fine system in full storage and fine PCG to 1e-6."""
+    sc = domino_full
+    ds = agipc.DeviceScene(sc)
+    ctx = ds.context()
+    fs = agipc.FineStep(ctx, ds, tol=1e-6)
+    fs.run()
+    assert ctx.status() == agipc.OK
+    got = fs.host()
+    frp, fci, fval = oracle.fine_system(sc)
+    assert np.array_equal(got["row_ptr"], frp) and np.array_equal(got["col"], fci)
+    assert np.linalg.norm(got["val"] - fval) <= VAL_RTOL * np.linalg.norm(fval)
+    res = oracle.spmv(frp, fci, fval, got["y"]) + sc.g
+    assert np.linalg.norm(res) <= 1.05e-6 * np.linalg.norm(sc.g)
+    ctx.close()
+
+
+# ------------------------------------------------------------------ status / edge cases
+
+
+def test_status_not_converged_and_zero_rhs():
+    sc = scenes.unit_cube(seed=1001)
+    ds = agipc.DeviceScene(sc)
+    ctx = ds.context()
+    step = agipc.CoarsenedStep(ctx, ds, tol=1e-12, max_iter=1)
+    step.run()
+    assert ctx.status() == agipc.ERR_NOT_CONVERGED
+    assert int(step.iters.item()) == 1
+    step.g_c.zero_()
+    step.solve()
+    assert ctx.status() == agipc.OK
+    assert int(step.iters.item()) == 0 and not step.y[: int(step.n_c.item())].any()
+    ctx.close()
+
+
+def test_status_bad_index_and_capacity():
+    sc = scenes.unit_cube(seed=1001)
+    ds = agipc.DeviceScene(sc)
+    ctx = ds.context()
+    bad = ds.edges.clone()
+    bad[7, 1] = sc.n + 5
+    labels = torch.empty(sc.n, dtype=torch.int32, device="cuda")
+    nc = torch.zeros(1, dtype=torch.int32, device="cuda")
+    agipc.agipc_aggregate(ctx, sc.n, bad, ds.tags, labels, nc)
+    assert ctx.status() == agipc.ERR_BAD_INDEX
+    step = agipc.CoarsenedStep(ctx, ds, tol=1e-8)
+    step.aggregate()
+    small_col = torch.empty(10, dtype=torch.int32, device="cuda")
+    small_val = torch.empty(10, 9, dtype=torch.float64, device="cuda")
+    agipc.agipc_assemble_coarse(ctx, ds.n, step.labels, step.n_c, ds.row_ptr, ds.col, ds.val, ds.pair_idx,
+                                ds.pair_blk, ds.g, step.row_ptr, small_col, small_val, step.nnz, step.g_c, step.dinv)
+    assert ctx.status() == agipc.ERR_CAPACITY
+    with pytest.raises(agipc.AgipcError):
+        agipc.agipc_aggregate(ctx, sc.n + 1, ds.edges, ds.tags, labels, nc)
+    ctx.close()
+
+
+def test_pcg_deterministic():
+    sc = scenes.unit_cube(seed=1001)
+    ds = agipc.DeviceScene(sc)
+    ctx = ds.context()
+    step = agipc.CoarsenedStep(ctx, ds, tol=1e-8)
+    step.run()
+    y1 = step.y.clone()
+    step.solve()
+    assert ctx.status() == agipc.OK
+    assert torch.equal(y1, step.y)
+    ctx.close()
