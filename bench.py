@@ -31,7 +31,10 @@ UNIT = "solves/s"
 TOL = 1e-6
 WORKLOAD = "domino_8x8: 64 StVK boxes of 6x12x24 Kuhn-split hexes (145,600 vertices, 663,552 tets), " \
            "200,000 PT/EE barrier stencils, 40-90% collapsible edges per box, FP64, PCG to 1e-6"
-KERNELS_PER_STEP = {"aggregate": 9, "assemble_coarse": 12, "pcg": 1, "prolongate": 1}
+KERNELS_PER_STEP = {"aggregate": 9, "assemble_coarse": 13, "pcg": 1, "prolongate": 1}
+# FP64 peak of a GB300 from its unit counts and clock: 152 SMs x 2 FP64 FMA per
+# clock x 2 flops x 2.07 GHz (a probe of dependent-free FMA streams reaches 1.20).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
 def _dist_env():
@@ -94,6 +97,29 @@ class ClockSampler:
         os.unlink(self.path)
         return {"sm_mhz": float(np.median(sms)) if sms else None, "sm_max_mhz": max(maxes) if maxes else None,
                 "samples": len(sms), "reasons": sorted(reasons)}
+
+
+def _traffic_record():
+    """DRAM bytes per launch of pcg_kernel from the committed ncu capture,
+    only while the kernel's source is the one that was captured."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "pcg_kernel_domino_8x8_coarse.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    h = hashlib.sha256()
+    for f in ("paper_2605_04773_gb300/csrc/pcg.cu", "paper_2605_04773_gb300/csrc/agipc_common.cuh"):
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    if h.hexdigest() != rec.get("source_sha256"):
+        return None
+    return rec["dram_bytes_read"] + rec["dram_bytes_write"]
+
+
+def pcg_flops_per_iter(nnzb: int, n: int) -> int:
+    """FP64 flops of one Chronopoulos-Gear PCG iteration: 9 FMAs per 3x3 block
+    (18 flops) and, per row, the p, s, x, r updates (4 x 3 FMAs), the 3x3
+    preconditioner (15 flops) and the gamma and rho dot products (2 x 3 FMAs)."""
+    return 18 * nnzb + (24 + 15 + 12) * n
 
 
 def pcg_bytes_per_iter(nnzb: int, n: int, elem: int = 8) -> int:
@@ -219,6 +245,8 @@ def run_ours(args):
         pcg_avg_s = float(np.mean(pcg_ms)) / 1e3
         pcg_bytes = iters * pcg_bytes_per_iter(nnz_c, n_c)
         achieved = pcg_bytes / pcg_avg_s / 1e9
+        pcg_flops = iters * pcg_flops_per_iter(nnz_c, n_c)
+        achieved_tf = pcg_flops / pcg_avg_s / 1e12
         fine_iters, fine_nnz = fres["iters"], fres["col"].size
         fine_pcg_bytes = fine_iters * pcg_bytes_per_iter(fine_nnz, sc.n)
         out = {
@@ -228,18 +256,24 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "n_fine": sc.n, "n_pairs": sc.n_pairs, "fine_upper_nnzb": sc.nnzb,
                        "tol": TOL, "seed": sc.seed, "l2": "flushed (256 MB write) before every timed step",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
-            "roofline": {"bound": "hbm", "kernel": "pcg_kernel (persistent, whole coarse solve)",
-                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "peak_kind": peak_kind, "traffic": None,
-                         "algorithmic_bytes_per_launch": pcg_bytes, "launch_ms": 1e3 * pcg_avg_s,
-                         "note": "coarse working set %.1f MB is L2-resident across iterations" %
-                                 (pcg_bytes_per_iter(nnz_c, n_c) / 1e6)},
+            "roofline": {"bound": "alu", "kernel": "pcg_kernel (persistent, whole coarse solve)",
+                         "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved_tf / FP64_PEAK_TFLOPS, "peak_kind": "derived (FP64 units x clock)",
+                         "traffic": _traffic_record(), "traffic_unit": "DRAM bytes per launch (ncu)",
+                         "algorithmic_flops_per_launch": pcg_flops,
+                         "launch_ms": 1e3 * pcg_avg_s,
+                         "hbm_view": {"algorithmic_bytes_per_launch": pcg_bytes, "achieved_gbs": achieved,
+                                      "peak_gbs": peak, "peak_kind": peak_kind, "frac": achieved / peak,
+                                      "note": "coarse working set %.1f MB per iteration is L2-resident" %
+                                              (pcg_bytes_per_iter(nnz_c, n_c) / 1e6)}},
             "coarse": {"n_c": n_c, "active_ratio": n_c / sc.n, "nnzb_c": nnz_c, "pcg_iters": iters,
                        "relres": res["relres"], "pcg_ms": 1e3 * pcg_avg_s,
                        "step_ms_median": float(np.median(step_ms))},
             "fine_pcg": {"value": 1e3 / float(np.median(fine_ms)), "unit": UNIT, "ms_per_step": float(np.median(fine_ms)),
                          "pcg_iters": fine_iters, "nnzb": fine_nnz, "relres": fres["relres"],
                          "hbm_gbs_pcg_algorithmic": fine_pcg_bytes / (float(np.median(fine_ms)) / 1e3) / 1e9,
+                         "fp64_tflops_pcg_algorithmic": fine_iters * pcg_flops_per_iter(fine_nnz, sc.n) /
+                                                         (float(np.median(fine_ms)) / 1e3) / 1e12,
                          "speedup_of_coarsened": float(np.median(fine_ms)) / (1e3 * total_s / args.steps)},
             "e2e": {"value": ws * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": sum(KERNELS_PER_STEP.values()) * args.steps,
@@ -300,7 +334,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -31,7 +31,7 @@ struct PcgScratch {
     int32_t *brow;              // [max_nnzb] row of every block
     uint8_t *rowflag;           // [max_rows] bit0: row split across warps, bit1: empty row
     double *partials;           // [2][max_grid][4]
-    unsigned *bar;              // [4]: arrival count, generation, bad-input flag, spare
+    unsigned *bar;              // [64]: [0] barrier arrivals, [32] bad-input flag (separate lines)
     int max_grid;
 };
 
@@ -80,51 +80,34 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
     return v;
 }
 
-__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v)
-{
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ unsigned atom_add_acqrel_u32(unsigned *p, unsigned v)
-{
-    unsigned old;
-    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-    return old;
-}
-
 __device__ __forceinline__ void set_status(uint32_t *status, uint32_t bit) { atomicOr(status, bit); }
 
 // --------------------------------------------------------------------------
-// Grid barrier for a cooperative (co-resident) launch.  Sense is a
-// generation counter; the last CTA to arrive resets the count and bumps the
-// generation.  Every wait is bounded: after kSpinLimit polls the CTA records
-// ST_TIMEOUT and the call returns false, so a kernel can wind down instead
-// of hanging.  bar[0] = arrivals, bar[1] = generation; both start at 0.
+// Grid barrier for a cooperative (co-resident) launch, on a per-launch
+// monotone arrival counter (zeroed before the launch): the k-th barrier of a
+// CTA waits until k * nblocks CTAs have arrived.  Release = fence.acq_rel +
+// relaxed add, acquire = polling load.  The wait is bounded: after
+// kSpinLimit polls the CTA records ST_TIMEOUT and the call returns false,
+// so the kernel winds down instead of hanging.
 // --------------------------------------------------------------------------
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, uint32_t *status)
+__device__ __forceinline__ bool grid_sync(unsigned *count, unsigned nblocks, unsigned &epoch, uint32_t *status)
 {
     __shared__ int s_ok;
     __syncthreads();
+    ++epoch;
     if (threadIdx.x == 0) {
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(count), "r"(1u) : "memory");
+        const unsigned target = epoch * nblocks;
         int ok = 1;
-        unsigned gen = ld_acquire_u32(bar + 1);
-        __threadfence();
-        unsigned arrived = atom_add_acqrel_u32(bar, 1u);
-        if (arrived == nblocks - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            st_release_u32(bar + 1, gen + 1);
-        } else {
-            long long spins = 0;
-            while (ld_acquire_u32(bar + 1) == gen) {
-                if (++spins > kSpinLimit) {
-                    set_status(status, ST_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
+        long long spins = 0;
+        while ((int)(ld_acquire_u32(count) - target) < 0) {
+            if (++spins > kSpinLimit) {
+                set_status(status, ST_TIMEOUT);
+                ok = 0;
+                break;
             }
         }
-        __threadfence();
         s_ok = ok;
     }
     __syncthreads();

@@ -7,6 +7,7 @@
 #include "agipc_common.cuh"
 
 int pcg_block_size();
+int pcg_smem_bytes();
 const void *pcg_kernel_ptr();
 int assemble_long_row_ctas();
 
@@ -48,7 +49,7 @@ void carve_all(agipc_ctx *c, char *base, size_t *total)
     c->pcg.brow = cv.take<int32_t>((size_t)c->max_nnzb);
     c->pcg.rowflag = cv.take<uint8_t>(n);
     c->pcg.partials = cv.take<double>(2 * (size_t)c->pcg.max_grid * 4);
-    c->pcg.bar = cv.take<unsigned>(4);
+    c->pcg.bar = cv.take<unsigned>(64);
     *total = cv.off;
 }
 
@@ -101,7 +102,10 @@ extern "C" int agipc_create(agipc_ctx **out, void *cuda_stream, int32_t max_fine
     // Persistent PCG: as many co-resident CTAs as the occupancy allows, capped
     // at two per SM (the grid barrier's cost grows with the CTA count).
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_kernel_ptr(), pcg_block_size(), 0) != cudaSuccess ||
+    if (cudaFuncSetAttribute(pcg_kernel_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, pcg_smem_bytes()) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_kernel_ptr(), pcg_block_size(), pcg_smem_bytes()) !=
+            cudaSuccess ||
         per_sm < 1) {
         delete c;
         return AGIPC_ERR_CUDA;

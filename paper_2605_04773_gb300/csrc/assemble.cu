@@ -19,12 +19,15 @@
 //   3. the set's keys are scattered into their rows and every row is sorted
 //      (warp bitonic sort for rows <= 32 blocks, shared-memory bitonic sort
 //      up to 8192, a column bitmap beyond).
-//   4. numeric: each term finds its upper position by binary search in the
-//      sorted row and adds its 3x3 block with FP64 atomics; warps whose 32
-//      terms share one key (the interior of a large super-node) first reduce
-//      with shuffles, mixed warps merge equal keys per match group.
-//   5. the lower triangle is written as transposes, diagonal blocks are
-//      symmetrised and inverted for the block-Jacobi preconditioner.
+//   4. numeric: lanes fold runs of consecutive terms with the same coarse key
+//      (the interior of a super-node) in registers and add each run to its
+//      upper position (binary search in the sorted row) with FP64 atomics,
+//      which execute in the L2; warps whose lanes all end on one key reduce
+//      it with shuffles first.  FP64 is slow on the SM of this part, so the
+//      SM only adds where a key repeats.
+//   5. the lower triangle is written as transposes; the diagonal blocks are
+//      symmetrised and inverted (thread per row) for the block-Jacobi
+//      preconditioner.
 //   6. g_c by atomics with the same warp merge.
 #include <algorithm>
 
@@ -307,6 +310,61 @@ __device__ __forceinline__ int64_t find_col(const int32_t *__restrict__ row_ptr,
     return (lo < row_ptr[row + 1] && col[lo] == c) ? lo : -1;
 }
 
+// Upper coarse block (lo, hi) = (min(a, b), max(a, b)) of term t and its
+// 3x3 value oriented for row lo (see the rules at the top of this file).
+__device__ __forceinline__ bool term_value(const TermArgs &A, int64_t t, int32_t nc, int32_t &lo, int32_t &hi,
+                                           double V[9])
+{
+    int32_t a, b;
+    bool off;
+    const double *blk;
+    if (!term_labels(A, t, nc, a, b, off, blk)) return false;
+    double B[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) B[e] = __ldg(blk + e);
+    if (a == b) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) V[3 * r + c] = off ? B[3 * r + c] + B[3 * c + r] : B[3 * r + c];
+    } else if (a < b) {
+#pragma unroll
+        for (int e = 0; e < 9; ++e) V[e] = B[e];
+    } else {
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) V[3 * r + c] = B[3 * c + r];
+    }
+    lo = min(a, b);
+    hi = max(a, b);
+    return true;
+}
+
+// Add a folded run to its coarse block with L2 atomics (the adds run in the
+// L2, not in the SM's FP64 unit).
+__device__ __forceinline__ void flush_run(unsigned long long key, const double acc[9], const int32_t *row_ptr,
+                                          const int32_t *col, int64_t cap, double *val, uint32_t *status)
+{
+    const int32_t lo = (int32_t)(key >> 32), hi = (int32_t)(key & 0xffffffffu);
+    const int64_t pos = find_col(row_ptr, col, lo, hi, cap);
+    if (pos < 0) {
+        set_status(status, pos == -2 ? ST_CAPACITY : ST_BAD_INDEX);
+        return;
+    }
+    double *dst = val + 9 * pos;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) atomicAdd(dst + e, acc[e]);
+}
+
+// Numeric phase.  A warp takes 32 x kRun consecutive terms; each lane folds
+// its kRun terms left to right, adding a term to the running block while the
+// coarse key repeats (the interior of a super-node) and flushing the run
+// with atomics when it changes.  If all 32 lanes end on the same key the warp
+// reduces it with shuffles first, so a large super-node's diagonal block
+// receives one atomic set per 32 x kRun terms instead of one per term.
+constexpr int kRun = 8;
+
 __global__ void __launch_bounds__(kTb) numeric_kernel(TermArgs A, const int32_t *__restrict__ row_ptr,
                                                       const int32_t *__restrict__ col, int64_t cap, double *val,
                                                       uint32_t *status)
@@ -314,77 +372,40 @@ __global__ void __launch_bounds__(kTb) numeric_kernel(TermArgs A, const int32_t 
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int32_t nc = *A.n_c_dev;
-    for (int64_t t0 = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * 32; t0 < A.n_terms; t0 += nwarps * 32) {
-        const int64_t t = t0 + lane;
+    const int64_t span = 32 * kRun;
+    for (int64_t t0 = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * span; t0 < A.n_terms;
+         t0 += nwarps * span) {
         unsigned long long key = kEmptyKey;
-        double V[9];
+        double acc[9];
 #pragma unroll
-        for (int e = 0; e < 9; ++e) V[e] = 0.0;
-        int32_t lo = 0, hi = 0;
-        if (t < A.n_terms) {
-            int32_t a, b;
-            bool off;
-            const double *blk;
-            if (term_labels(A, t, nc, a, b, off, blk)) {
-                double B[9];
+        for (int e = 0; e < 9; ++e) acc[e] = 0.0;
+        for (int j = 0; j < kRun; ++j) {
+            const int64_t t = t0 + (int64_t)lane * kRun + j;
+            if (t >= A.n_terms) break;
+            int32_t lo, hi;
+            double V[9];
+            if (!term_value(A, t, nc, lo, hi, V)) {
+                set_status(status, ST_BAD_INDEX);
+                continue;
+            }
+            const unsigned long long k = pack_key(lo, hi);
+            if (k == key) {
 #pragma unroll
-                for (int e = 0; e < 9; ++e) B[e] = __ldg(blk + e);
-                if (a == b) {
+                for (int e = 0; e < 9; ++e) acc[e] += V[e];
+            } else {
+                if (key != kEmptyKey) flush_run(key, acc, row_ptr, col, cap, val, status);
+                key = k;
 #pragma unroll
-                    for (int r = 0; r < 3; ++r)
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) V[3 * r + c] = off ? B[3 * r + c] + B[3 * c + r] : B[3 * r + c];
-                } else if (a < b) {
-#pragma unroll
-                    for (int e = 0; e < 9; ++e) V[e] = B[e];
-                } else {
-#pragma unroll
-                    for (int r = 0; r < 3; ++r)
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) V[3 * r + c] = B[3 * c + r];
-                }
-                lo = min(a, b);
-                hi = max(a, b);
-                key = pack_key(lo, hi);
+                for (int e = 0; e < 9; ++e) acc[e] = V[e];
             }
         }
         const unsigned same = __match_any_sync(kFull, key);
-        const bool uniform = __all_sync(kFull, same == kFull) && key != kEmptyKey;
-        bool owner;
-        if (uniform) {
-            // one key for the whole warp: tree reduction, lane 0 adds
+        if (same == kFull && key != kEmptyKey) {
 #pragma unroll
-            for (int e = 0; e < 9; ++e) V[e] = warp_sum(V[e]);
-            owner = lane == 0;
-        } else if (__any_sync(kFull, __popc(same) > 1 && key != kEmptyKey)) {
-            // merge each match group into its lowest lane
-            const int leader = __ffs(same) - 1;
-            double acc[9];
-#pragma unroll
-            for (int e = 0; e < 9; ++e) acc[e] = V[e];
-            for (int src = 0; src < 32; ++src) {
-                const bool take = ((same >> src) & 1u) && src != lane && leader == lane;
-#pragma unroll
-                for (int e = 0; e < 9; ++e) {
-                    const double o = __shfl_sync(kFull, V[e], src);
-                    if (take) acc[e] += o;
-                }
-            }
-#pragma unroll
-            for (int e = 0; e < 9; ++e) V[e] = acc[e];
-            owner = leader == lane;
-        } else {
-            owner = true;
-        }
-        if (owner && key != kEmptyKey) {
-            const int64_t pos = find_col(row_ptr, col, lo, hi, cap);
-            if (pos < 0) {
-                set_status(status, pos == -2 ? ST_CAPACITY : ST_BAD_INDEX);
-            } else {
-                double *dst = val + 9 * pos;
-#pragma unroll
-                for (int e = 0; e < 9; ++e) atomicAdd(dst + e, V[e]);
-            }
+            for (int e = 0; e < 9; ++e) acc[e] = warp_sum(acc[e]);
+            if (lane == 0) flush_run(key, acc, row_ptr, col, cap, val, status);
+        } else if (key != kEmptyKey) {
+            flush_run(key, acc, row_ptr, col, cap, val, status);
         }
     }
 }
@@ -409,9 +430,10 @@ __device__ __forceinline__ bool inverse3(const double *A, double *R)
     return true;
 }
 
-__global__ void mirror_dinv_kernel(const int32_t *__restrict__ n_c_dev, const int32_t *__restrict__ row_ptr,
-                                   const int32_t *__restrict__ col, int64_t cap, double *val, double *__restrict__ dinv,
-                                   uint32_t *status)
+// Lower triangle = transpose of the upper one (warp per coarse row; pure
+// data movement).
+__global__ void mirror_kernel(const int32_t *__restrict__ n_c_dev, const int32_t *__restrict__ row_ptr,
+                              const int32_t *__restrict__ col, int64_t cap, double *val, uint32_t *status)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -419,48 +441,60 @@ __global__ void mirror_dinv_kernel(const int32_t *__restrict__ n_c_dev, const in
     for (int64_t a = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; a < nc; a += nwarps) {
         const int32_t k0 = row_ptr[a], k1 = row_ptr[a + 1];
         if (k1 > cap) continue;
-        bool has_diag = false;
         for (int32_t k = k0 + lane; k < k1; k += 32) {
             const int32_t b = col[k];
+            if (b >= a) break;  // columns ascend: the rest is the diagonal and the upper part
+            const int64_t q = find_col(row_ptr, col, b, (int32_t)a, cap);
+            if (q < 0) { set_status(status, q == -2 ? ST_CAPACITY : ST_BAD_INDEX); continue; }
+            const double *src = val + 9 * q;
             double *dst = val + 9 * (int64_t)k;
-            if (b < a) {
-                const int64_t q = find_col(row_ptr, col, b, (int32_t)a, cap);
-                if (q < 0) { set_status(status, q == -2 ? ST_CAPACITY : ST_BAD_INDEX); continue; }
-                const double *src = val + 9 * q;
-                double T[9];
+            double T[9];
 #pragma unroll
-                for (int r = 0; r < 3; ++r)
+            for (int r = 0; r < 3; ++r)
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) T[3 * r + c] = src[3 * c + r];
+                for (int c = 0; c < 3; ++c) T[3 * r + c] = src[3 * c + r];
 #pragma unroll
-                for (int e = 0; e < 9; ++e) dst[e] = T[e];
-            } else if (b == a) {
-                has_diag = true;
-                double D[9];
-#pragma unroll
-                for (int e = 0; e < 9; ++e) D[e] = dst[e];
-                D[3] = D[1];
-                D[6] = D[2];
-                D[7] = D[5];
-#pragma unroll
-                for (int e = 0; e < 9; ++e) dst[e] = D[e];
-                double R[9];
-                bool ok = inverse3(D, R);
-#pragma unroll
-                for (int e = 0; e < 9; ++e) ok = ok && isfinite(R[e]);
-                if (!ok) {
-                    set_status(status, ST_NONFINITE);
-#pragma unroll
-                    for (int e = 0; e < 9; ++e) R[e] = 0.0;
-                }
-#pragma unroll
-                for (int e = 0; e < 9; ++e) dinv[9 * a + e] = R[e];
-            }
+            for (int e = 0; e < 9; ++e) dst[e] = T[e];
         }
-        if (!__any_sync(kFull, has_diag)) {
-            if (lane == 0) set_status(status, ST_NONFINITE);
-            if (lane < 9) dinv[9 * a + lane] = 0.0;
+    }
+}
+
+// Diagonal blocks: symmetrise (lower from upper) and invert for the
+// block-Jacobi preconditioner; one thread per coarse row, so every FP64
+// instruction runs with a full warp.
+__global__ void dinv_kernel(const int32_t *__restrict__ n_c_dev, const int32_t *__restrict__ row_ptr,
+                            const int32_t *__restrict__ col, int64_t cap, double *val, double *__restrict__ dinv,
+                            uint32_t *status)
+{
+    const int32_t nc = *n_c_dev;
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < nc; a += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = find_col(row_ptr, col, (int32_t)a, (int32_t)a, cap);
+        double R[9];
+        bool ok = q >= 0;
+        if (ok) {
+            double *d = val + 9 * q;
+            double D[9];
+#pragma unroll
+            for (int e = 0; e < 9; ++e) D[e] = d[e];
+            D[3] = D[1];
+            D[6] = D[2];
+            D[7] = D[5];
+            d[3] = D[3];
+            d[6] = D[6];
+            d[7] = D[7];
+            ok = inverse3(D, R);
+#pragma unroll
+            for (int e = 0; e < 9; ++e) ok = ok && isfinite(R[e]);
+        } else if (q == -2) {
+            set_status(status, ST_CAPACITY);
         }
+        if (!ok) {
+            if (q != -2) set_status(status, ST_NONFINITE);
+#pragma unroll
+            for (int e = 0; e < 9; ++e) R[e] = 0.0;
+        }
+#pragma unroll
+        for (int e = 0; e < 9; ++e) dinv[9 * a + e] = R[e];
     }
 }
 
@@ -552,9 +586,13 @@ extern "C" int agipc_assemble_coarse(agipc_ctx *ctx, int32_t n_fine, const int32
                                                        coarse_row_ptr, coarse_col, coarse_cap_nnzb, ctx->bitmap,
                                                        ctx->bitmap_words);
     zero_outputs_kernel<<<grid_sm, kTb, 0, st>>>(n_coarse_dev, coarse_nnzb_dev, coarse_cap_nnzb, coarse_val, g_c);
-    numeric_kernel<<<gt, kTb, 0, st>>>(A, coarse_row_ptr, coarse_col, coarse_cap_nnzb, coarse_val, ctx->status);
-    mirror_dinv_kernel<<<gw, kTb, 0, st>>>(n_coarse_dev, coarse_row_ptr, coarse_col, coarse_cap_nnzb, coarse_val, dinv,
-                                           ctx->status);
+    const unsigned gnum = (unsigned)std::min<int64_t>(div_up(n_terms > 0 ? n_terms : 1, (int64_t)kTb * kRun),
+                                                      (int64_t)grid_sm * 4);
+    numeric_kernel<<<gnum, kTb, 0, st>>>(A, coarse_row_ptr, coarse_col, coarse_cap_nnzb, coarse_val, ctx->status);
+    mirror_kernel<<<gw, kTb, 0, st>>>(n_coarse_dev, coarse_row_ptr, coarse_col, coarse_cap_nnzb, coarse_val,
+                                      ctx->status);
+    dinv_kernel<<<(unsigned)std::min<int64_t>(div_up(n_fine, kTb), (int64_t)grid_sm * 4), kTb, 0, st>>>(
+        n_coarse_dev, coarse_row_ptr, coarse_col, coarse_cap_nnzb, coarse_val, dinv, ctx->status);
     gradient_kernel<<<(unsigned)std::min<int64_t>(div_up(n_fine, kTb), (int64_t)grid_sm * 4), kTb, 0, st>>>(
         n_fine, labels, n_coarse_dev, g, g_c, ctx->status);
     return cudaPeekAtLastError() == cudaSuccess ? AGIPC_OK : AGIPC_ERR_CUDA;

@@ -9,25 +9,52 @@
 //     u = M^-1 r,  w = A u,  gamma = (r,u),  delta = (w,u)
 //     beta = gamma/gamma_old,  alpha = gamma/(delta - beta*gamma/alpha_old)
 //     p = u + beta p,  s = w + beta s,  x += alpha p,  r -= alpha s
-// Per iteration the kernel runs two phases separated by grid barriers:
-//   S: w = A u (nnz-balanced: every warp owns an equal, 32-aligned slice of
-//      the blocks; the warp stages its 32 blocks (2304 B) in shared memory
-//      with coalesced 16-byte loads, multiplies, and reduces rows with a
-//      segmented shuffle scan; rows cut by a slice boundary are added with
-//      atomics) and the partial delta = sum over blocks of u_row^T B u_col;
-//   P: the row-local updates above, the preconditioner and the partial
-//      gamma/rho of the next iteration.
-// Partial sums go to a per-CTA slot and every CTA reduces all slots in the
-// same order, so the scalars are bitwise identical in every CTA and from run
-// to run.  Barrier waits are bounded (ST_TIMEOUT).
+//
+// GB300 design.  FP64 on this part runs at ~1.9 operations per clock per SM
+// and one FP64 warp instruction occupies the SM's FP64 unit for ~19 cycles
+// whatever its active mask (65-cycle dependent latency), so the kernel
+// counts FP64 warp instructions: a 3x3 block costs 9 FMAs and everything
+// else per block, per row and per reduction is kept small next to that.
+//   S phase (w = A u): the blocks are cut into slices of 160 (32 lanes x 5
+//     consecutive blocks); slices go round-robin to warps spread over all
+//     CTAs.  Each warp owns two shared-memory buffers for its slices, filled
+//     by cp.async copies: when the matrix fits in shared memory (at most one
+//     slice per warp) the slice is loaded once and stays resident for the
+//     whole solve; otherwise the next slice (also the first slice of the next
+//     iteration) streams in while the current one is multiplied.  Each lane
+//     accumulates its 5 blocks in registers, one accumulator per row segment;
+//     segments that cross lanes are joined by the lane where the row starts.
+//     Column gathers of u, u of the lane's rows (for delta) and the rows'
+//     split flags are all issued together, so emitting a row never waits on a
+//     load.  A row inside one slice is stored; a row cut by a slice boundary
+//     is added with FP64 atomics (w of such rows is zeroed in the P phase).
+//   P phase: rows are split evenly over the CTAs; each thread does the
+//     row-local updates, the 3x3 preconditioner and its share of gamma, rho.
+//   CTA sums go through shared memory, one warp per summed value; CTA
+//     partials go to per-CTA slots and every CTA reduces all slots in the
+//     same order (again one warp per value), so the scalars are bitwise
+//     identical in every CTA and from run to run; one thread does the
+//     divisions.
+//   Each phase ends in a grid barrier (monotone arrival counter, bounded
+//     spin).
 #include <algorithm>
 
 #include "agipc_common.cuh"
 
 namespace {
 
-constexpr int kPcgBlock = 512;
+constexpr int kPcgBlock = 256;
 constexpr int kPcgWarps = kPcgBlock / 32;
+constexpr int kK = 5;                          // consecutive blocks per lane
+constexpr int kSlice = 32 * kK;                // blocks per warp slice
+constexpr int kValBytes = kSlice * 9 * 8;      // 11520
+constexpr int kIdxBytes = kSlice * 4;          // 640 per index array
+constexpr int kBufBytes = kValBytes + 2 * kIdxBytes;
+constexpr int kJoinBytes = 32 * (3 * 8 + 3 * 4);
+constexpr int kWarpSmem = 2 * kBufBytes + kJoinBytes;
+constexpr int kPartBytes = kPcgBlock * 3 * 8;
+constexpr int kPcgSmem = kPcgWarps * kWarpSmem + kPartBytes;
+constexpr int kMaxGridLanes = 8;               // the grid reduction handles up to 256 CTAs
 
 struct PcgArgs {
     const int32_t *n_dev;
@@ -48,61 +75,252 @@ struct PcgArgs {
     uint32_t *status;
 };
 
-// Sum two values over the CTA; thread 0 receives the totals (fixed order).
-__device__ __forceinline__ void block_sum2(double &a, double &b, double (*s_red)[4])
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src, int src_bytes)
 {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    a = warp_sum(a);
-    b = warp_sum(b);
-    if (lane == 0) { s_red[wid][0] = a; s_red[wid][1] = b; }
-    __syncthreads();
-    if (wid == 0) {
-        a = lane < kPcgWarps ? s_red[lane][0] : 0.0;
-        b = lane < kPcgWarps ? s_red[lane][1] : 0.0;
-        a = warp_sum(a);
-        b = warp_sum(b);
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gmem_src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Copy slice `sl` (values, columns, rows) into a warp buffer; zero-fills
+// past the last block so no byte beyond the arrays is read.
+__device__ __forceinline__ void issue_slice(unsigned char *buf, int64_t sl, int64_t nnz, const double *val,
+                                            const int32_t *col, const int32_t *brow, int lane)
+{
+    const int64_t base = sl * kSlice;
+    const int cnt = (int)min64(kSlice, nnz - base);
+    const int vbytes = 72 * cnt, ibytes = 4 * cnt;
+    const unsigned char *vs = reinterpret_cast<const unsigned char *>(val + 9 * base);
+    const unsigned char *cs = reinterpret_cast<const unsigned char *>(col + base);
+    const unsigned char *rs = reinterpret_cast<const unsigned char *>(brow + base);
+    for (int q = lane; 16 * q < vbytes; q += 32) cp_async16(buf + 16 * q, vs + 16 * q, min(16, vbytes - 16 * q));
+    for (int q = lane; 16 * q < ibytes; q += 32) {
+        cp_async16(buf + kValBytes + 16 * q, cs + 16 * q, min(16, ibytes - 16 * q));
+        cp_async16(buf + kValBytes + kIdxBytes + 16 * q, rs + 16 * q, min(16, ibytes - 16 * q));
     }
-    __syncthreads();
 }
 
-__device__ __forceinline__ void emit_row(double *w, const uint8_t *rowflag, int row, double y0, double y1, double y2)
+// Sum of N values per thread over the CTA: threads park their values in
+// shared memory, warp 0 adds them with a tree (3 levels over the 8 warps,
+// then 5 shuffle levels).  The result is valid in thread 0.
+template <int N>
+__device__ __forceinline__ void cta_sum(double (&v)[N], double *s_part, double *s_out)
+{
+    // Warp k adds value k (each warp sits on its own SM sub-partition, whose
+    // FP64 pipe is the bottleneck): 3 tree levels over the 8 warps' slots,
+    // then 5 shuffle levels.  Totals land in s_out[0..N) for every thread.
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < N; ++k) s_part[N * threadIdx.x + k] = v[k];
+    __syncthreads();
+    if (wid < N) {
+        double t[kPcgWarps];
+#pragma unroll
+        for (int q = 0; q < kPcgWarps; ++q) t[q] = s_part[N * (lane + 32 * q) + wid];
+#pragma unroll
+        for (int h = kPcgWarps / 2; h > 0; h >>= 1)
+#pragma unroll
+            for (int q = 0; q < h; ++q) t[q] += t[q + h];
+        const double tot = warp_sum(t[0]);
+        if (lane == 0) s_out[wid] = tot;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[k] = s_out[k];
+}
+
+__device__ __forceinline__ void store_row(double *w, int row, bool split, const double y[3])
 {
     double *dst = w + 3 * (int64_t)row;
-    if (rowflag[row] & 1) {
-        atomicAdd(dst, y0);
-        atomicAdd(dst + 1, y1);
-        atomicAdd(dst + 2, y2);
+    if (split) {
+        atomicAdd(dst, y[0]);
+        atomicAdd(dst + 1, y[1]);
+        atomicAdd(dst + 2, y[2]);
     } else {
-        dst[0] = y0;
-        dst[1] = y1;
-        dst[2] = y2;
+        dst[0] = y[0];
+        dst[1] = y[1];
+        dst[2] = y[2];
     }
 }
 
-__global__ void __launch_bounds__(kPcgBlock) pcg_kernel(PcgArgs A)
+__device__ __forceinline__ double dsel(bool c, double a, double b)
 {
-    __shared__ __align__(16) double s_stage[kPcgWarps][9 * 32];
-    __shared__ double s_red[kPcgWarps][4];
-    __shared__ double s_scal[4];
+    // select on the bit pattern: integer moves, no FP64 instruction
+    return __longlong_as_double(c ? __double_as_longlong(a) : __double_as_longlong(b));
+}
+
+// w = A u over one slice held in `buf` (rows inside the slice) or += (rows
+// cut by its ends); adds this lane's share of delta to dpart.
+//
+// Per lane the 5 blocks are folded left to right into one running row
+// accumulator (reset at a row change by a select, so the FP64 work is
+// exactly 9 FMAs per block with no divergence); a row segment's total is the
+// accumulator at the segment's last block.  delta takes u_row . total at
+// each segment end.  Segments that cross lanes are joined by the lane where
+// the row starts, which walks forward over the lanes that continue it.
+__device__ __forceinline__ void slice_spmv(const unsigned char *buf, int cnt, const double *u, double *w,
+                                           const uint8_t *rowflag, unsigned char *join, int lane, double &dpart)
+{
+    const double *s_val = reinterpret_cast<const double *>(buf);
+    const int32_t *s_col = reinterpret_cast<const int32_t *>(buf + kValBytes);
+    const int32_t *s_row = reinterpret_cast<const int32_t *>(buf + kValBytes + kIdxBytes);
+    int rows_[kK];
+    double xv[kK][3];
+    double ur[kK][3];
+    bool split[kK];
+#pragma unroll
+    for (int j = 0; j < kK; ++j) {
+        const int q = lane * kK + j;
+        rows_[j] = -1;
+        split[j] = false;
+        xv[j][0] = xv[j][1] = xv[j][2] = 0.0;
+        ur[j][0] = ur[j][1] = ur[j][2] = 0.0;
+        if (q < cnt) {
+            const int rj = s_row[q];
+            rows_[j] = rj;
+            const double *uc = u + 3 * (int64_t)s_col[q];
+            xv[j][0] = __ldcg(uc);
+            xv[j][1] = __ldcg(uc + 1);
+            xv[j][2] = __ldcg(uc + 2);
+            if (j == 0 || rj != s_row[q - 1]) {  // first block of a row segment
+                const double *up = u + 3 * (int64_t)rj;
+                ur[j][0] = __ldcg(up);
+                ur[j][1] = __ldcg(up + 1);
+                ur[j][2] = __ldcg(up + 2);
+                split[j] = (__ldcg(rowflag + rj) & 1) != 0;
+            }
+        }
+    }
+    // running accumulator; segment bookkeeping by selects
+    double acc[3] = {0.0, 0.0, 0.0};
+    double fa[3] = {0.0, 0.0, 0.0}, la[3] = {0.0, 0.0, 0.0};
+    int fr = -1, lr = -1;
+    bool f_split = false, l_split = false, s_cur = false, first_open = true;
+    double cu[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int j = 0; j < kK; ++j) {
+        const bool valid = rows_[j] >= 0;
+        const bool start = valid && (j == 0 || rows_[j] != rows_[j - 1]);
+        const bool end = valid && (j == kK - 1 || rows_[j + 1] != rows_[j]);
+        const double *B = s_val + 9 * (lane * kK + j);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            cu[c] = dsel(start, ur[j][c], cu[c]);
+            acc[c] = dsel(start, 0.0, acc[c]);
+            acc[c] = fma(B[3 * c + 2], xv[j][2], fma(B[3 * c + 1], xv[j][1], fma(B[3 * c], xv[j][0], acc[c])));
+        }
+        s_cur = start ? split[j] : s_cur;
+        // delta: u_row . segment total at every segment end (zero elsewhere)
+        dpart = fma(dsel(end, cu[0], 0.0), acc[0], fma(dsel(end, cu[1], 0.0), acc[1], fma(dsel(end, cu[2], 0.0), acc[2], dpart)));
+        if (end) {
+            const bool last = j == kK - 1 || rows_[j + 1] < 0;
+            if (first_open) {                       // the lane's first segment: joined below
+                fr = rows_[j]; f_split = s_cur;
+                fa[0] = acc[0]; fa[1] = acc[1]; fa[2] = acc[2];
+                first_open = false;
+            } else if (last) {                      // the lane's last segment: joined below
+                lr = rows_[j]; l_split = s_cur;
+                la[0] = acc[0]; la[1] = acc[1]; la[2] = acc[2];
+            } else {                                // a row wholly inside this lane
+                store_row(w, rows_[j], s_cur, acc);
+            }
+        }
+    }
+    const bool single = lr < 0;
+    double *s_fa = reinterpret_cast<double *>(join);
+    int32_t *s_fr = reinterpret_cast<int32_t *>(join + 32 * 24);
+    int32_t *s_single = s_fr + 32;
+    int32_t *s_last = s_fr + 64;
+    s_fr[lane] = fr;
+    s_single[lane] = single ? 1 : 0;
+    s_last[lane] = single ? fr : lr;
+    s_fa[3 * lane] = fa[0];
+    s_fa[3 * lane + 1] = fa[1];
+    s_fa[3 * lane + 2] = fa[2];
+    __syncwarp();
+    if (!single) {
+        for (int q = lane + 1; q < 32 && s_fr[q] == lr; ++q) {
+            la[0] += s_fa[3 * q]; la[1] += s_fa[3 * q + 1]; la[2] += s_fa[3 * q + 2];
+            if (!s_single[q]) break;
+        }
+        store_row(w, lr, l_split, la);
+    }
+    if (fr >= 0 && (lane == 0 || s_last[lane - 1] != fr)) {
+        if (single) {
+            for (int q = lane + 1; q < 32 && s_fr[q] == fr; ++q) {
+                fa[0] += s_fa[3 * q]; fa[1] += s_fa[3 * q + 1]; fa[2] += s_fa[3 * q + 2];
+                if (!s_single[q]) break;
+            }
+        }
+        store_row(w, fr, f_split, fa);
+    }
+    __syncwarp();
+}
+
+// Row-local update of one row i: p = u + beta p, s = w + beta s,
+// x += alpha p, r -= alpha s, u = M^-1 r; returns gamma, rho shares.
+__device__ __forceinline__ void row_update(int64_t i, const double uu[3], const double ww[3], double pp[3], double ss[3],
+                                           double rr[3], const double xx[3], const double D[9], double alpha, double beta,
+                                           double *p, double *s, double *r, double *x, double *u, double *w,
+                                           bool zero_w, double &gpart, double &rpart)
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        pp[c] = fma(beta, pp[c], uu[c]);
+        ss[c] = fma(beta, ss[c], ww[c]);
+        x[3 * i + c] = fma(alpha, pp[c], xx[c]);
+        rr[c] = fma(-alpha, ss[c], rr[c]);
+        p[3 * i + c] = pp[c];
+        s[3 * i + c] = ss[c];
+        r[3 * i + c] = rr[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double uc = fma(D[3 * c + 2], rr[2], fma(D[3 * c + 1], rr[1], D[3 * c] * rr[0]));
+        u[3 * i + c] = uc;
+        gpart = fma(rr[c], uc, gpart);
+        rpart = fma(rr[c], rr[c], rpart);
+    }
+    if (zero_w) {
+        w[3 * i] = 0.0;
+        w[3 * i + 1] = 0.0;
+        w[3 * i + 2] = 0.0;
+    }
+}
+
+__global__ void __launch_bounds__(kPcgBlock, 1) pcg_kernel(PcgArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double s_scal[2];
+    __shared__ double s_tot[4];
+    __shared__ double s_grid[3];
+    __shared__ int s_dec;
 
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const unsigned nblocks = gridDim.x;
-    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t nthreads = (int64_t)nblocks * blockDim.x;
-    const int64_t gwarp = (int64_t)blockIdx.x * kPcgWarps + wib;
     const int64_t nwarps = (int64_t)nblocks * kPcgWarps;
+    const int64_t gwarp = (int64_t)wib * nblocks + blockIdx.x;  // slices interleave over CTAs
+    const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
 
     const int32_t n = *A.n_dev;
-    if (n < 0 || n > A.max_rows) {
-        if (tid == 0) set_status(A.status, ST_BAD_INDEX);
+    if (n < 0 || n > A.max_rows || nblocks > 32 * kMaxGridLanes) {
+        if (gtid == 0) set_status(A.status, ST_BAD_INDEX);
         return;
     }
     const int64_t nnz = A.rp[n];
     if (nnz < 0 || nnz > A.max_nnzb) {
-        if (tid == 0) set_status(A.status, nnz < 0 ? ST_BAD_INDEX : ST_CAPACITY);
+        if (gtid == 0) set_status(A.status, nnz < 0 ? ST_BAD_INDEX : ST_CAPACITY);
         return;
     }
-    const int64_t chunk = max64(32, div_up(div_up(nnz, nwarps), 32) * 32);
+    const int64_t nslices = div_up(nnz, kSlice);
+    const bool resident = nslices <= nwarps;  // every warp keeps at most one slice in shared memory
+    // rows owned by this CTA in the row-local phases
+    const int64_t rows_per_cta = div_up(n, nblocks);
+    const int64_t row0 = min64((int64_t)blockIdx.x * rows_per_cta, n);
+    const int64_t row1 = min64(row0 + rows_per_cta, n);
+    const bool one_row = rows_per_cta <= kPcgBlock;  // row state can be fetched ahead of the barrier
 
     double *__restrict__ r = A.S.r;
     double *u = A.S.u;
@@ -113,21 +331,26 @@ __global__ void __launch_bounds__(kPcgBlock) pcg_kernel(PcgArgs A)
     int32_t *brow = A.S.brow;
     uint8_t *rowflag = A.S.rowflag;
     double *partials = A.S.partials;
+    unsigned *count = A.S.bar;
     const int pstride = A.S.max_grid * 4;
+    unsigned epoch = 0;
+    unsigned char *wbuf = smem + (size_t)wib * kWarpSmem;
+    unsigned char *join = wbuf + 2 * kBufBytes;
+    double *s_part = reinterpret_cast<double *>(smem + (size_t)kPcgWarps * kWarpSmem);
 
     // ---- setup: block rows, split flags, x = 0, r = b, u = M^-1 r, p = s = w = 0
     double gpart = 0.0, rpart = 0.0;
-    for (int64_t i = tid; i < n; i += nthreads) {
+    for (int64_t i = row0 + threadIdx.x; i < row1; i += blockDim.x) {
         const int32_t k0 = A.rp[i], k1 = A.rp[i + 1];
         bool bad = k0 < 0 || k1 < k0 || k1 > nnz;
         for (int32_t k = k0; !bad && k < k1; ++k) {
             brow[k] = (int32_t)i;
             bad = (unsigned)A.col[k] >= (unsigned)n;
         }
-        if (bad) atomicOr(A.S.bar + 2, 1u);
+        if (bad) atomicOr(A.S.bar + 32, 1u);
         uint8_t f = 0;
         if (k1 == k0) f = 2;
-        else if (k0 / chunk != (k1 - 1) / chunk) f = 1;
+        else if (k0 / kSlice != (k1 - 1) / kSlice) f = 1;
         rowflag[i] = f;
         double rr[3];
 #pragma unroll
@@ -148,19 +371,28 @@ __global__ void __launch_bounds__(kPcgBlock) pcg_kernel(PcgArgs A)
             rpart += rr[c] * rr[c];
         }
     }
-    block_sum2(gpart, rpart, s_red);
-    if (threadIdx.x == 0) {
-        partials[blockIdx.x * 4 + 0] = gpart;
-        partials[blockIdx.x * 4 + 1] = rpart;
+    {
+        double v[2] = {gpart, rpart};
+        cta_sum<2>(v, s_part, s_tot);
+        if (threadIdx.x == 0) {
+            partials[blockIdx.x * 4 + 0] = v[0];
+            partials[blockIdx.x * 4 + 1] = v[1];
+        }
     }
-    bool ok = grid_barrier(A.S.bar, nblocks, A.status);
-    if (ok && ld_acquire_u32(A.S.bar + 2) != 0u) {
+    bool ok = grid_sync(count, nblocks, epoch, A.status);
+    if (ok && ld_acquire_u32(A.S.bar + 32) != 0u) {
         // a row pointer or column index out of range: nothing gathers through it
-        if (tid == 0) set_status(A.status, ST_BAD_INDEX);
+        if (gtid == 0) set_status(A.status, ST_BAD_INDEX);
         ok = false;
     }
+    // The warp's first slice goes to buffer 0 (brow is complete after the
+    // barrier).  Invariant: each iteration's first slice sits in buffer nb.
+    int nb = 0;
+    if (ok && gwarp < nslices) issue_slice(wbuf, gwarp, nnz, A.val, A.col, brow, lane);
+    cp_async_commit();
 
-    double alpha_old = 1.0, gamma_old = 1.0, bnorm = 0.0, rnorm = 0.0;
+    double alpha_old = 1.0, gamma_old = 1.0, bnorm2 = 0.0, rnorm2 = 0.0;
+    const double tol2 = A.tol * A.tol;
     int32_t it = 0;
     bool converged = false;
     while (ok) {
@@ -168,150 +400,147 @@ __global__ void __launch_bounds__(kPcgBlock) pcg_kernel(PcgArgs A)
         double *part = partials + par * pstride;
         // ---- S phase: w = A u, partial delta
         double dpart = 0.0;
-        {
-            double *stage = s_stage[wib];
-            const int64_t kb = gwarp * chunk;
-            const int64_t ke = min64(kb + chunk, nnz);
-            int carry_row = -1;
-            double c0 = 0.0, c1 = 0.0, c2 = 0.0;
-            for (int64_t base = kb; base < ke; base += 32) {
-                const int cnt = (int)min64(32, ke - base);
-                const int nd = 9 * cnt;
-                const double2 *src = reinterpret_cast<const double2 *>(A.val + 9 * base);
-                double2 *dst2 = reinterpret_cast<double2 *>(stage);
-                for (int q = lane; q < (nd >> 1); q += 32) dst2[q] = __ldg(src + q);
-                if ((nd & 1) && lane == 0) stage[nd - 1] = __ldg(A.val + 9 * base + nd - 1);
-                __syncwarp();
-                int row = -1;
-                double y0 = 0.0, y1 = 0.0, y2 = 0.0;
-                if (lane < cnt) {
-                    const int64_t k = base + lane;
-                    row = __ldcg(brow + k);
-                    const int32_t cj = __ldg(A.col + k);
-                    const double *B = stage + 9 * lane;
-                    const double x0 = __ldcg(u + 3 * (int64_t)cj), x1 = __ldcg(u + 3 * (int64_t)cj + 1),
-                                 x2 = __ldcg(u + 3 * (int64_t)cj + 2);
-                    y0 = B[0] * x0 + B[1] * x1 + B[2] * x2;
-                    y1 = B[3] * x0 + B[4] * x1 + B[5] * x2;
-                    y2 = B[6] * x0 + B[7] * x1 + B[8] * x2;
-                    dpart += __ldcg(u + 3 * (int64_t)row) * y0 + __ldcg(u + 3 * (int64_t)row + 1) * y1 +
-                             __ldcg(u + 3 * (int64_t)row + 2) * y2;
-                }
-                __syncwarp();
-                // segmented suffix sums: rows are non-decreasing across lanes
+        for (int64_t sl = gwarp; sl < nslices; sl += nwarps) {
+            if (!resident) {
+                // stream the next slice of this iteration, or the first slice of
+                // the next one, into the other buffer while this one is used
+                const int64_t next = sl + nwarps < nslices ? sl + nwarps : gwarp;
+                issue_slice(wbuf + (nb ^ 1) * kBufBytes, next, nnz, A.val, A.col, brow, lane);
+                cp_async_commit();
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncwarp();
+            const int cnt = (int)min64(kSlice, nnz - sl * kSlice);
+            slice_spmv(wbuf + nb * kBufBytes, cnt, u, w, rowflag, join, lane, dpart);
+            if (!resident) nb ^= 1;
+        }
+        // one row per thread: fetch the row's own state now, so that only w
+        // (written by other CTAs) is read after the barrier
+        const int64_t my_row = row0 + threadIdx.x;
+        const bool has_row = one_row && my_row < row1;
+        double ru[3], rp_[3], rs[3], rr_[3], rx[3], rD[9], rw[3];
+        if (has_row) {
 #pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    const double n0 = __shfl_down_sync(kFull, y0, off);
-                    const double n1 = __shfl_down_sync(kFull, y1, off);
-                    const double n2 = __shfl_down_sync(kFull, y2, off);
-                    const int nr = __shfl_down_sync(kFull, row, off);
-                    if (lane + off < 32 && nr == row) { y0 += n0; y1 += n1; y2 += n2; }
-                }
-                const int prev = __shfl_up_sync(kFull, row, 1);
-                const bool head = row >= 0 && (lane == 0 || prev != row);
-                if (lane == 0) {
-                    if (carry_row >= 0 && carry_row == row) { y0 += c0; y1 += c1; y2 += c2; }
-                    else if (carry_row >= 0) emit_row(w, rowflag, carry_row, c0, c1, c2);
-                }
-                const unsigned heads = __ballot_sync(kFull, head);
-                const int last = 31 - __clz(heads);
-                if (head && lane != last) emit_row(w, rowflag, row, y0, y1, y2);
-                carry_row = __shfl_sync(kFull, row, last);
-                c0 = __shfl_sync(kFull, y0, last);
-                c1 = __shfl_sync(kFull, y1, last);
-                c2 = __shfl_sync(kFull, y2, last);
+            for (int c = 0; c < 3; ++c) {
+                ru[c] = __ldcg(u + 3 * my_row + c);
+                rp_[c] = p[3 * my_row + c];
+                rs[c] = s[3 * my_row + c];
+                rr_[c] = r[3 * my_row + c];
+                rx[c] = x[3 * my_row + c];
             }
-            if (lane == 0 && carry_row >= 0) emit_row(w, rowflag, carry_row, c0, c1, c2);
+#pragma unroll
+            for (int e = 0; e < 9; ++e) rD[e] = A.dinv[9 * my_row + e];
         }
         {
-            double dummy = 0.0;
-            block_sum2(dpart, dummy, s_red);
-            if (threadIdx.x == 0) part[blockIdx.x * 4 + 2] = dpart;
+            double v[1] = {dpart};
+            cta_sum<1>(v, s_part, s_tot);
+            if (threadIdx.x == 0) part[blockIdx.x * 4 + 2] = v[0];
         }
-        if (!grid_barrier(A.S.bar, nblocks, A.status)) { ok = false; break; }
+        if (!grid_sync(count, nblocks, epoch, A.status)) { ok = false; break; }
+        if (has_row) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) rw[c] = __ldcg(w + 3 * my_row + c);
+        }
 
-        // ---- global scalars, reduced identically in every CTA
-        if (wib == 0) {
-            double g = 0.0, rh = 0.0, dl = 0.0;
-            for (unsigned k = lane; k < nblocks; k += 32) {
-                g += __ldcg(part + k * 4 + 0);
-                rh += __ldcg(part + k * 4 + 1);
-                dl += __ldcg(part + k * 4 + 2);
+        // ---- global scalars: every CTA reduces all slots in the same order;
+        // thread 0 alone does the FP64 divisions and square root.
+        if (wib < 3) {
+            // warp k reduces scalar k of all CTAs (fixed order)
+            double pv[kMaxGridLanes];
+#pragma unroll
+            for (int q = 0; q < kMaxGridLanes; ++q) {
+                const unsigned k = lane + 32 * q;
+                pv[q] = k < nblocks ? __ldcg(part + k * 4 + wib) : 0.0;
             }
-            g = warp_sum(g);
-            rh = warp_sum(rh);
-            dl = warp_sum(dl);
-            if (lane == 0) { s_scal[0] = g; s_scal[1] = rh; s_scal[2] = dl; }
+#pragma unroll
+            for (int h = kMaxGridLanes / 2; h > 0; h >>= 1)
+#pragma unroll
+                for (int q = 0; q < h; ++q) pv[q] += pv[q + h];
+            const double tot = warp_sum(pv[0]);
+            if (lane == 0) s_grid[wib] = tot;
         }
         __syncthreads();
-        const double gamma = s_scal[0], rho = s_scal[1], delta = s_scal[2];
+        if (threadIdx.x == 0) {
+            const double g = s_grid[0], rh = s_grid[1], dl = s_grid[2];
+            // 0 iterate, 1 converged, 2 iteration cap, 3 non-finite.  The test
+            // ||r|| <= tol ||b|| is done on squares; alpha needs one division:
+            // g / (dl - beta g / alpha_old) with beta = g / gamma_old equals
+            // g t / (dl t - g^2), t = gamma_old alpha_old.
+            int decision = 0;
+            double alpha = 0.0, beta = 0.0;
+            rnorm2 = rh;
+            if (it == 0) bnorm2 = rh;
+            if (!isfinite(rh) || !isfinite(g) || !isfinite(dl)) decision = 3;
+            else if (bnorm2 == 0.0 || rh <= tol2 * bnorm2) decision = 1;
+            else if (it >= A.max_iter) decision = 2;
+            else {
+                if (it == 0) {
+                    alpha = g / dl;
+                } else {
+                    const double t = gamma_old * alpha_old;
+                    beta = g / gamma_old;
+                    alpha = (g * t) / fma(dl, t, -g * g);
+                }
+                if (!isfinite(alpha) || !isfinite(beta)) decision = 3;
+                gamma_old = g;
+                alpha_old = alpha;
+            }
+            s_scal[0] = alpha;
+            s_scal[1] = beta;
+            s_dec = decision;
+        }
         __syncthreads();
-        rnorm = sqrt(rho);
-        if (it == 0) bnorm = rnorm;
-        if (!isfinite(rho) || !isfinite(gamma) || !isfinite(delta)) {
-            if (tid == 0) set_status(A.status, ST_NONFINITE);
+        const double alpha = s_scal[0], beta = s_scal[1];
+        const int decision = s_dec;
+        __syncthreads();
+        if (decision == 3) {
+            if (gtid == 0) set_status(A.status, ST_NONFINITE);
             break;
         }
-        if (bnorm == 0.0 || rnorm <= A.tol * bnorm) { converged = true; break; }
-        if (it >= A.max_iter) break;
-        const double beta = it == 0 ? 0.0 : gamma / gamma_old;
-        const double alpha = it == 0 ? gamma / delta : gamma / (delta - beta * gamma / alpha_old);
-        if (!isfinite(alpha) || !isfinite(beta)) {
-            if (tid == 0) set_status(A.status, ST_NONFINITE);
-            break;
-        }
+        if (decision == 1) { converged = true; break; }
+        if (decision == 2) break;
 
         // ---- P phase: row-local updates, preconditioner, next partials
         double *npart = partials + (par ^ 1) * pstride;
         gpart = 0.0;
         rpart = 0.0;
-        for (int64_t i = tid; i < n; i += nthreads) {
-            double uu[3], ww[3], pp[3], ss[3], rr[3];
+        if (one_row) {
+            if (has_row) row_update(my_row, ru, rw, rp_, rs, rr_, rx, rD, alpha, beta, p, s, r, x, u, w,
+                                    rowflag[my_row] != 0, gpart, rpart);
+        } else {
+            for (int64_t i = row0 + threadIdx.x; i < row1; i += blockDim.x) {
+                double uu[3], ww[3], pp[3], ss[3], rr[3], xx[3], D[9];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                uu[c] = __ldcg(u + 3 * i + c);
-                ww[c] = __ldcg(w + 3 * i + c);
-                pp[c] = p[3 * i + c];
-                ss[c] = s[3 * i + c];
-                rr[c] = r[3 * i + c];
-            }
+                for (int c = 0; c < 3; ++c) {
+                    uu[c] = __ldcg(u + 3 * i + c);
+                    ww[c] = __ldcg(w + 3 * i + c);
+                    pp[c] = p[3 * i + c];
+                    ss[c] = s[3 * i + c];
+                    rr[c] = r[3 * i + c];
+                    xx[c] = x[3 * i + c];
+                }
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                pp[c] = uu[c] + beta * pp[c];
-                ss[c] = ww[c] + beta * ss[c];
-                x[3 * i + c] += alpha * pp[c];
-                rr[c] -= alpha * ss[c];
-                p[3 * i + c] = pp[c];
-                s[3 * i + c] = ss[c];
-                r[3 * i + c] = rr[c];
-            }
-            const double *D = A.dinv + 9 * i;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const double uc = D[3 * c] * rr[0] + D[3 * c + 1] * rr[1] + D[3 * c + 2] * rr[2];
-                u[3 * i + c] = uc;
-                gpart += rr[c] * uc;
-                rpart += rr[c] * rr[c];
-            }
-            if (rowflag[i]) {
-                w[3 * i] = 0.0;
-                w[3 * i + 1] = 0.0;
-                w[3 * i + 2] = 0.0;
+                for (int e = 0; e < 9; ++e) D[e] = A.dinv[9 * i + e];
+                row_update(i, uu, ww, pp, ss, rr, xx, D, alpha, beta, p, s, r, x, u, w, rowflag[i] != 0, gpart, rpart);
             }
         }
-        block_sum2(gpart, rpart, s_red);
-        if (threadIdx.x == 0) {
-            npart[blockIdx.x * 4 + 0] = gpart;
-            npart[blockIdx.x * 4 + 1] = rpart;
+        {
+            double v[2] = {gpart, rpart};
+            cta_sum<2>(v, s_part, s_tot);
+            if (threadIdx.x == 0) {
+                npart[blockIdx.x * 4 + 0] = v[0];
+                npart[blockIdx.x * 4 + 1] = v[1];
+            }
         }
-        gamma_old = gamma;
-        alpha_old = alpha;
         ++it;
-        if (!grid_barrier(A.S.bar, nblocks, A.status)) { ok = false; break; }
+        if (!grid_sync(count, nblocks, epoch, A.status)) { ok = false; break; }
     }
-    if (tid == 0 && (ok || it > 0)) {
+    cp_async_wait<0>();
+    if (gtid == 0 && (ok || it > 0)) {
         *A.iters_dev = it;
-        *A.relres_dev = bnorm > 0.0 ? rnorm / bnorm : 0.0;
+        *A.relres_dev = bnorm2 > 0.0 ? sqrt(rnorm2 / bnorm2) : 0.0;
         if (ok && !converged) set_status(A.status, ST_NOT_CONVERGED);
     }
 }
@@ -319,6 +548,7 @@ __global__ void __launch_bounds__(kPcgBlock) pcg_kernel(PcgArgs A)
 }  // namespace
 
 int pcg_block_size() { return kPcgBlock; }
+int pcg_smem_bytes() { return kPcgSmem; }
 
 const void *pcg_kernel_ptr() { return reinterpret_cast<const void *>(&pcg_kernel); }
 
@@ -331,8 +561,8 @@ extern "C" int agipc_pcg(agipc_ctx *ctx, int32_t max_rows, const int32_t *n_rows
         return AGIPC_ERR_INVALID_ARG;
     if (!(opt->tol >= 0.0) || opt->max_iter < 0 || (opt->rhs_sign != 1 && opt->rhs_sign != -1))
         return AGIPC_ERR_INVALID_ARG;
-    if (((uintptr_t)val & 15u) != 0 || ((uintptr_t)dinv & 7u) != 0 || ((uintptr_t)b & 7u) != 0 ||
-        ((uintptr_t)x & 7u) != 0)
+    if (((uintptr_t)val & 15u) != 0 || ((uintptr_t)col & 15u) != 0 || ((uintptr_t)dinv & 7u) != 0 ||
+        ((uintptr_t)b & 7u) != 0 || ((uintptr_t)x & 7u) != 0)
         return AGIPC_ERR_INVALID_ARG;
     PcgArgs A;
     A.n_dev = n_rows_dev;
@@ -351,9 +581,9 @@ extern "C" int agipc_pcg(agipc_ctx *ctx, int32_t max_rows, const int32_t *n_rows
     A.relres_dev = relres_dev;
     A.S = ctx->pcg;
     A.status = ctx->status;
-    if (cudaMemsetAsync(ctx->pcg.bar, 0, 4 * sizeof(unsigned), ctx->stream) != cudaSuccess) return AGIPC_ERR_CUDA;
+    if (cudaMemsetAsync(ctx->pcg.bar, 0, 64 * sizeof(unsigned), ctx->stream) != cudaSuccess) return AGIPC_ERR_CUDA;
     void *args[] = {&A};
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)pcg_kernel, dim3((unsigned)ctx->pcg_grid),
-                                                dim3(kPcgBlock), args, 0, ctx->stream);
+                                                dim3(kPcgBlock), args, kPcgSmem, ctx->stream);
     return e == cudaSuccess ? AGIPC_OK : AGIPC_ERR_CUDA;
 }
