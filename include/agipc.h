@@ -158,6 +158,33 @@ int agipc_pcg(agipc_ctx *ctx, int32_t max_rows, const int32_t *n_rows_dev, const
  */
 int agipc_prolongate(agipc_ctx *ctx, int32_t n_fine, const int32_t *labels, const double *y, double *dx);
 
+/*
+ * Labeller without allocation.  The paper has no counterpart: this is a
+ * convenience of this library.  It computes exactly what agipc_aggregate
+ * computes, for callers that cannot allocate GPU memory - code that has no
+ * agipc_ctx because agipc_create must cudaMalloc its scratch arena, e.g. a
+ * plugin that only receives device pointers from its host application, or a
+ * simulation loop whose memory manager forbids cudaMalloc after start-up.
+ *   cuda_stream        cudaStream_t to enqueue on (NULL = legacy default stream)
+ *   n_fine, n_edges, edges, tags, labels, n_coarse_dev   as agipc_aggregate
+ *   status_dev         out: caller-owned device uint32; set to 0 by the call,
+ *                      then to a nonzero bit pattern if the GPU met an
+ *                      out-of-range edge endpoint or a bounded wait ran out
+ * Scratch is one fixed array of AGIPC_AGGREGATE_STATIC_MAX_NODES-sized
+ * buffers (about 12 MiB) compiled into the library's device image, so every
+ * GPU that loads the library holds it until the process exits.  n_fine above
+ * that maximum is rejected with AGIPC_ERR_INVALID_ARG before anything is
+ * enqueued.  The first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  The call never calls cudaMalloc or cudaFree.  All calls
+ * share the one array: calls that overlap on the GPU (different streams, no
+ * ordering between them) race and corrupt each other's results; serialize
+ * them.  The array keeps the previous call's contents, which no call reads.
+ */
+#define AGIPC_AGGREGATE_STATIC_MAX_NODES (1 << 20)
+int agipc_aggregate_static(void *cuda_stream, int32_t n_fine, int64_t n_edges, const int32_t *edges,
+                           const uint8_t *tags, int32_t *labels, int32_t *n_coarse_dev, uint32_t *status_dev);
+
 /* Synchronize the context's stream; return (and clear) the first device-side
  * error recorded since the last call, or AGIPC_OK. */
 int agipc_status(agipc_ctx *ctx);

@@ -66,10 +66,11 @@ def load():
     lib.agipc_pcg.argtypes = [P, i32, P, P, P, P, P, P, P, ctypes.POINTER(_PcgOptions), P, P]
     lib.agipc_prolongate.argtypes = [P, i32, P, P, P]
     lib.agipc_status.argtypes = [P]
+    lib.agipc_aggregate_static.argtypes = [P, i32, i64, P, P, P, P, P]
     lib.agipc_status_string.argtypes = [ctypes.c_int]
     lib.agipc_status_string.restype = ctypes.c_char_p
     for name in ("agipc_create", "agipc_destroy", "agipc_set_stream", "agipc_aggregate", "agipc_assemble_coarse",
-                 "agipc_pcg", "agipc_prolongate", "agipc_status"):
+                 "agipc_pcg", "agipc_prolongate", "agipc_status", "agipc_aggregate_static"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -161,6 +162,19 @@ def agipc_pcg(ctx: Context, max_rows: int, n_rows_dev, row_ptr, col, val, dinv, 
 
 def agipc_prolongate(ctx: Context, n_fine: int, labels, y, dx):
     _check(load().agipc_prolongate(ctx.handle, int(n_fine), _ptr(labels), _ptr(y), _ptr(dx)), "agipc_prolongate")
+
+
+AGGREGATE_STATIC_MAX_NODES = 1 << 20
+
+
+def agipc_aggregate_static(stream, n_fine: int, edges, tags, labels, n_coarse_dev, status_dev):
+    """The labeller for callers that cannot allocate GPU memory (no Context):
+    its scratch is a fixed array inside the library, so n_fine is limited to
+    AGGREGATE_STATIC_MAX_NODES and calls that overlap on the GPU race.
+    status_dev (uint32 device scalar) receives the device-side error bits."""
+    _check(load().agipc_aggregate_static(ctypes.c_void_p(stream.cuda_stream), int(n_fine), int(edges.shape[0]),
+                                         _ptr(edges), _ptr(tags), _ptr(labels), _ptr(n_coarse_dev),
+                                         _ptr(status_dev)), "agipc_aggregate_static")
 
 
 # ---------------------------------------------------------------------------

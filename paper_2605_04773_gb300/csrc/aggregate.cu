@@ -166,3 +166,74 @@ extern "C" int agipc_aggregate(agipc_ctx *ctx, int32_t n_fine, int64_t n_edges, 
     agg_relabel_kernel<<<gn, tb, 0, st>>>(n_fine, ctx->parent, ctx->rank, labels);
     return cudaPeekAtLastError() == cudaSuccess ? AGIPC_OK : AGIPC_ERR_CUDA;
 }
+
+// ---------------------------------------------------------------------------
+// agipc_aggregate_static: the labeller for callers that cannot allocate GPU
+// memory.  Its scratch lives in a fixed array in the library's device image
+// instead of an agipc_ctx arena (whose creation calls cudaMalloc).
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+constexpr int64_t kStaticAggNodes = AGIPC_AGGREGATE_STATIC_MAX_NODES;
+// parent [N] + group hashes [N] + ranks [N + 1] + scan partials, in 32-bit words
+constexpr int64_t kStaticAggWords = 3 * kStaticAggNodes + 1 + kScanMaxParts;
+
+// Every GPU that loads the library holds this array (about 12 MiB) until the
+// process exits.  Host code must not take its address directly: on the host
+// the name is only a stand-in, so the device address comes from
+// cudaGetSymbolAddress.
+static __device__ __align__(256) int32_t g_static_agg_scratch[kStaticAggWords];
+
+std::mutex g_static_agg_mutex;
+int32_t *g_static_agg_ptr[256];  // device address of the array, per device
+
+}  // namespace
+
+extern "C" int agipc_aggregate_static(void *cuda_stream, int32_t n_fine, int64_t n_edges, const int32_t *edges,
+                                      const uint8_t *tags, int32_t *labels, int32_t *n_coarse_dev,
+                                      uint32_t *status_dev)
+{
+    if (n_fine < 0 || n_edges < 0 || n_fine > kStaticAggNodes) return AGIPC_ERR_INVALID_ARG;
+    if ((n_fine > 0 && !labels) || !n_coarse_dev || !status_dev || (n_edges > 0 && (!edges || !tags)))
+        return AGIPC_ERR_INVALID_ARG;
+    if (((uintptr_t)edges & 7u) != 0) return AGIPC_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return AGIPC_ERR_CUDA;
+    int32_t *scratch = nullptr;
+    {
+        // first call on this device: look the array's device address up once
+        std::lock_guard<std::mutex> lock(g_static_agg_mutex);
+        if (!g_static_agg_ptr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_static_agg_scratch) != cudaSuccess || !p) return AGIPC_ERR_CUDA;
+            g_static_agg_ptr[dev] = static_cast<int32_t *>(p);
+        }
+        scratch = g_static_agg_ptr[dev];
+    }
+    int32_t *parent = scratch;
+    uint32_t *ghash = reinterpret_cast<uint32_t *>(scratch + kStaticAggNodes);
+    int32_t *rank = scratch + 2 * kStaticAggNodes;
+    int32_t *parts = scratch + 3 * kStaticAggNodes + 1;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    // The array keeps the previous call's contents; every word this call
+    // reads is written by this call first, and the status starts at zero.
+    if (cudaMemsetAsync(status_dev, 0, sizeof(uint32_t), st) != cudaSuccess) return AGIPC_ERR_CUDA;
+    if (n_fine == 0) {
+        if (cudaMemsetAsync(n_coarse_dev, 0, sizeof(int32_t), st) != cudaSuccess) return AGIPC_ERR_CUDA;
+        return AGIPC_OK;
+    }
+    const int tb = 256;
+    const unsigned gn = (unsigned)div_up(n_fine, tb);
+    const unsigned ge = (unsigned)(n_edges > 0 ? div_up(n_edges, tb) : 1);
+    const unsigned gg = (unsigned)div_up(div_up(n_fine, 32) * 32, tb);
+    agg_init_kernel<<<gn, tb, 0, st>>>(n_fine, ghash);
+    if (n_edges > 0) agg_group_edges_kernel<<<ge, tb, 0, st>>>(n_fine, n_edges, edges, tags, ghash, status_dev);
+    agg_group_close_kernel<<<gg, tb, 0, st>>>(n_fine, ghash, parent);
+    if (n_edges > 0) agg_union_kernel<<<ge, tb, 0, st>>>(n_fine, n_edges, edges, tags, parent, status_dev);
+    agg_compress_kernel<<<gn, tb, 0, st>>>(n_fine, parent, rank);
+    if (!scan_exclusive_i32(rank, rank, n_fine, n_coarse_dev, parts, st)) return AGIPC_ERR_INVALID_ARG;
+    agg_relabel_kernel<<<gn, tb, 0, st>>>(n_fine, parent, rank, labels);
+    return cudaPeekAtLastError() == cudaSuccess ? AGIPC_OK : AGIPC_ERR_CUDA;
+}
