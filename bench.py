@@ -233,6 +233,13 @@ def run_ours(args):
     e2e_s = e0.elapsed_time(e1) / 1e3
     ctx.check()
 
+    # ---- precision form (FP32 blocks/SpMV/preconditioner, FP64 dots and
+    # residual replacement every 20 iterations, small-gap stencils in FP64) on
+    # the same workload with 1% of the barrier gaps redrawn below 0.05 dhat
+    prec = None
+    if not args.skip_forms:
+        prec = precision_form(ctx_factory=lambda d: d.context(), dev=dev, steps=min(args.steps, 20))
+
     # ---- max over ranks
     if ws > 1:
         t = torch.tensor([total_s, e2e_s], dtype=torch.float64, device=dev)
@@ -278,6 +285,7 @@ def run_ours(args):
             "e2e": {"value": ws * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": sum(KERNELS_PER_STEP.values()) * args.steps,
             "clocks": clocks,
+            "precision_form": prec,
             "wall_s_timed_region": t_wall,
         }
         if ws == 1 and not args.no_cpu_baseline:
@@ -286,6 +294,63 @@ def run_ours(args):
     ctx.close()
     if ws > 1:
         dist.destroy_process_group()
+
+
+def precision_form(ctx_factory, dev, steps: int):
+    """Time the precision form and measure its error against the FP64 path."""
+    import scipy.sparse
+    import torch
+    from paper_2605_04773_gb300 import agipc, scenes
+    sc = scenes.domino_grid(seed=1003, small_gap_frac=0.01)
+    md = agipc.MixedDeviceScene(sc, dev)
+    ctx = ctx_factory(md)
+    stream = torch.cuda.current_stream(dev)
+    mixed = agipc.MixedStep(ctx, md, tol=TOL)
+    full = agipc.CoarsenedStep(ctx, md, tol=TOL)
+    for _ in range(3):
+        mixed.run()
+    ctx.check()
+    l2 = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in ev:
+        l2.fill_(1.0)
+        a.record(stream)
+        mixed.run()
+        b.record(stream)
+    torch.cuda.synchronize(dev)
+    ctx.check()
+    ms = float(np.median([a.elapsed_time(b) for a, b in ev]))
+    m = mixed.host()
+    full.run()
+    ctx.check()
+    f = full.host()
+    # errors against the FP64 path on the unrounded inputs
+    gc, y32, crp, cci, cval = f["g_c"], m["y"], f["row_ptr"], f["col"], f["val"]
+    Hc = scipy.sparse.bsr_matrix((cval, cci, crp), shape=(3 * f["n_c"], 3 * f["n_c"]))
+    res32 = np.linalg.norm(Hc @ y32.ravel() + gc.ravel()) / np.linalg.norm(gc)
+    fine = agipc.FineStep(ctx, md, tol=TOL)
+    fine.inner.assemble()
+    ctx.check()
+    fh = fine.inner
+    nnz = int(fh.nnz.item())
+    Hf = scipy.sparse.bsr_matrix((fh.val[:nnz].cpu().numpy().reshape(-1, 3, 3), fh.col[:nnz].cpu().numpy(),
+                                  fh.row_ptr.cpu().numpy()), shape=(3 * sc.n, 3 * sc.n))
+    g = sc.g.ravel()
+
+    def dE(dx):
+        dx = dx.ravel()
+        return float(g @ dx + 0.5 * dx @ (Hf @ dx))
+
+    e64, e32 = dE(f["dx"]), dE(m["dx"])
+    pi = scenes.precision_inputs(sc)
+    ctx.close()
+    return {"value": 1e3 / ms, "unit": UNIT, "ms_per_step": ms, "pcg_iters": m["iters"], "workload":
+            "domino_8x8 with 1% of barrier gaps in (0.01, 0.05) dhat (seed 1003), tol 1e-6, refinement every 20",
+            "fp64_stencils": int(pi["pair_idx64"].shape[0]),
+            "dx_rel_err_vs_fp64": float(np.linalg.norm(m["dx"] - f["dx"]) / np.linalg.norm(f["dx"])),
+            "coarse_fp64_residual": float(res32), "fp64_path_residual": f["relres"],
+            "energy_decrease_fp64": e64, "energy_decrease_mixed": e32,
+            "energy_decrease_rel_err": abs(e32 - e64) / abs(e64)}
 
 
 def cpu_baseline(sc, reps: int = 1):
@@ -338,6 +403,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-forms", action="store_true", help="only the headline step (profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -153,6 +153,38 @@ int agipc_pcg(agipc_ctx *ctx, int32_t max_rows, const int32_t *n_rows_dev, const
               const agipc_pcg_options *opt, int32_t *iters_dev, double *relres_dev);
 
 /*
+ * Precision form of the coarse assembly: as agipc_assemble_coarse, with the
+ * fine blocks and most barrier stencils given in FP32 and the stencils of
+ * small gaps (whose stiffness FP32 would round too coarsely) given in FP64
+ * as a second list.  Every contribution is accumulated in FP64 into
+ * coarse_val (the FP64 master, used for residual replacement); coarse_val32
+ * and dinv32 receive its FP32 rounding and the FP32 rounding of the FP64
+ * block-Jacobi inverses.  Capacities and statuses as agipc_assemble_coarse
+ * (the pair count limit applies to n_pairs32 + n_pairs64).
+ */
+int agipc_assemble_coarse_mixed(agipc_ctx *ctx, int32_t n_fine, const int32_t *labels, const int32_t *n_coarse_dev,
+                                const int32_t *fine_row_ptr, const int32_t *fine_col, const float *fine_val32,
+                                int64_t fine_nnzb, int64_t n_pairs32, const int32_t *pair_idx32,
+                                const float *pair_blk32, int64_t n_pairs64, const int32_t *pair_idx64,
+                                const double *pair_blk64, const double *g, int32_t *coarse_row_ptr,
+                                int32_t *coarse_col, double *coarse_val, float *coarse_val32, int64_t coarse_cap_nnzb,
+                                int32_t *coarse_nnzb_dev, double *g_c, float *dinv32);
+
+/*
+ * Precision form of the PCG: the 3x3 blocks (val32), the SpMV and the
+ * block-Jacobi preconditioner (dinv32) run in FP32; the dot products are
+ * accumulated in FP64; x and r stay in FP64 and every refine_every
+ * iterations r is replaced by b - A x computed with the FP64 master matrix
+ * `val` (same structure), so the answer is that of the FP64 system.
+ * refine_every = 0 disables the replacement.  Other arguments, layouts and
+ * statuses as agipc_pcg.  val and val32 must be 16-byte aligned.
+ */
+int agipc_pcg_mixed(agipc_ctx *ctx, int32_t max_rows, const int32_t *n_rows_dev, const int32_t *row_ptr,
+                    const int32_t *col, const double *val, const float *val32, const float *dinv32, const double *b,
+                    double *x, const agipc_pcg_options *opt, int32_t refine_every, int32_t *iters_dev,
+                    double *relres_dev);
+
+/*
  * Prolongation d_f = U^T d_c (Sec. 4.3): dx[f] = y[labels[f]].
  *   n_fine, labels [n_fine], y [n_c][3]  ->  dx [n_fine][3]
  */

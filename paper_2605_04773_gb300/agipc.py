@@ -67,10 +67,14 @@ def load():
     lib.agipc_prolongate.argtypes = [P, i32, P, P, P]
     lib.agipc_status.argtypes = [P]
     lib.agipc_aggregate_static.argtypes = [P, i32, i64, P, P, P, P, P]
+    lib.agipc_assemble_coarse_mixed.argtypes = [P, i32, P, P, P, P, P, i64, i64, P, P, i64, P, P, P, P, P, P, P, i64,
+                                                P, P, P]
+    lib.agipc_pcg_mixed.argtypes = [P, i32, P, P, P, P, P, P, P, P, ctypes.POINTER(_PcgOptions), i32, P, P]
     lib.agipc_status_string.argtypes = [ctypes.c_int]
     lib.agipc_status_string.restype = ctypes.c_char_p
     for name in ("agipc_create", "agipc_destroy", "agipc_set_stream", "agipc_aggregate", "agipc_assemble_coarse",
-                 "agipc_pcg", "agipc_prolongate", "agipc_status", "agipc_aggregate_static"):
+                 "agipc_pcg", "agipc_prolongate", "agipc_status", "agipc_aggregate_static",
+                 "agipc_assemble_coarse_mixed", "agipc_pcg_mixed"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -162,6 +166,25 @@ def agipc_pcg(ctx: Context, max_rows: int, n_rows_dev, row_ptr, col, val, dinv, 
 
 def agipc_prolongate(ctx: Context, n_fine: int, labels, y, dx):
     _check(load().agipc_prolongate(ctx.handle, int(n_fine), _ptr(labels), _ptr(y), _ptr(dx)), "agipc_prolongate")
+
+
+def agipc_assemble_coarse_mixed(ctx: Context, n_fine: int, labels, n_coarse_dev, fine_row_ptr, fine_col, fine_val32,
+                                pair_idx32, pair_blk32, pair_idx64, pair_blk64, g, coarse_row_ptr, coarse_col,
+                                coarse_val, coarse_val32, coarse_nnzb_dev, g_c, dinv32):
+    _check(load().agipc_assemble_coarse_mixed(
+        ctx.handle, int(n_fine), _ptr(labels), _ptr(n_coarse_dev), _ptr(fine_row_ptr), _ptr(fine_col),
+        _ptr(fine_val32), int(fine_col.shape[0]), int(pair_idx32.shape[0]), _ptr(pair_idx32), _ptr(pair_blk32),
+        int(pair_idx64.shape[0]), _ptr(pair_idx64), _ptr(pair_blk64), _ptr(g), _ptr(coarse_row_ptr), _ptr(coarse_col),
+        _ptr(coarse_val), _ptr(coarse_val32), int(coarse_col.shape[0]), _ptr(coarse_nnzb_dev), _ptr(g_c),
+        _ptr(dinv32)), "agipc_assemble_coarse_mixed")
+
+
+def agipc_pcg_mixed(ctx: Context, max_rows: int, n_rows_dev, row_ptr, col, val, val32, dinv32, b, x, tol: float,
+                    max_iter: int, rhs_sign: int, refine_every: int, iters_dev, relres_dev):
+    opt = _PcgOptions(float(tol), int(max_iter), int(rhs_sign))
+    _check(load().agipc_pcg_mixed(ctx.handle, int(max_rows), _ptr(n_rows_dev), _ptr(row_ptr), _ptr(col), _ptr(val),
+                                  _ptr(val32), _ptr(dinv32), _ptr(b), _ptr(x), ctypes.byref(opt), int(refine_every),
+                                  _ptr(iters_dev), _ptr(relres_dev)), "agipc_pcg_mixed")
 
 
 AGGREGATE_STATIC_MAX_NODES = 1 << 20
@@ -259,6 +282,52 @@ class CoarsenedStep:
                     g_c=self.g_c[:nc].cpu().numpy(), dinv=self.dinv[:nc].cpu().numpy().reshape(-1, 3, 3),
                     y=self.y[:nc].cpu().numpy(), dx=self.dx.cpu().numpy(), iters=int(self.iters.item()),
                     relres=float(self.relres.item()))
+
+
+class MixedDeviceScene(DeviceScene):
+    """DeviceScene plus the precision form's inputs (FP32 blocks and stencils,
+    FP64 small-gap stencils)."""
+
+    def __init__(self, sc, device="cuda", fp64_gap: float = 0.05):
+        super().__init__(sc, device)
+        from . import scenes
+        pi = scenes.precision_inputs(sc, fp64_gap)
+        t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(device=device, dtype=dt)  # noqa: E731
+        self.val32 = t(pi["val32"].reshape(-1, 9), torch.float32)
+        self.pair_idx32 = t(pi["pair_idx32"].reshape(-1, 4), torch.int32)
+        self.pair_blk32 = t(pi["pair_blk32"].reshape(-1, 90), torch.float32)
+        self.pair_idx64 = t(pi["pair_idx64"].reshape(-1, 4), torch.int32)
+        self.pair_blk64 = t(pi["pair_blk64"].reshape(-1, 90), torch.float64)
+
+
+class MixedStep(CoarsenedStep):
+    """The precision form of the step: FP32 blocks, SpMV and preconditioner,
+    FP64 dot products, FP64 residual replacement every refine_every
+    iterations against the FP64 master coarse matrix."""
+
+    def __init__(self, ctx: Context, ds: MixedDeviceScene, tol: float, max_iter: int = 100000,
+                 refine_every: int = 20):
+        super().__init__(ctx, ds, tol, max_iter)
+        self.refine_every = refine_every
+        self.val32 = torch.empty(ds.capacity, 9, device=ds.g.device, dtype=torch.float32)
+        self.dinv32 = torch.empty(ds.n, 9, device=ds.g.device, dtype=torch.float32)
+
+    def assemble(self):
+        ds = self.ds
+        agipc_assemble_coarse_mixed(self.ctx, ds.n, self.labels, self.n_c, ds.row_ptr, ds.col, ds.val32,
+                                    ds.pair_idx32, ds.pair_blk32, ds.pair_idx64, ds.pair_blk64, ds.g, self.row_ptr,
+                                    self.col, self.val, self.val32, self.nnz, self.g_c, self.dinv32)
+
+    def solve(self):
+        agipc_pcg_mixed(self.ctx, self.ds.n, self.n_c, self.row_ptr, self.col, self.val, self.val32, self.dinv32,
+                        self.g_c, self.y, self.tol, self.max_iter, -1, self.refine_every, self.iters, self.relres)
+
+    def host(self):
+        out = super().host()
+        nnz = out["col"].size
+        out["val32"] = self.val32[:nnz].cpu().numpy().reshape(-1, 3, 3)
+        out["dinv32"] = self.dinv32[:out["n_c"]].cpu().numpy().reshape(-1, 3, 3)
+        return out
 
 
 class FineStep:

@@ -64,6 +64,7 @@ struct agipc_ctx {
     int32_t *long_rows;   // [max_n + 1]; [max_n] holds the count
     uint32_t *bitmap;     // [kLongRowCtas][bitmap_words]
     int64_t bitmap_words;
+    double *dinv64;       // [max_n][9] FP64 inverses before rounding (precision form)
 
     PcgScratch pcg;
     int pcg_block;

@@ -9,6 +9,7 @@
 int pcg_block_size();
 int pcg_smem_bytes();
 const void *pcg_kernel_ptr();
+const void *pcg_mixed_kernel_ptr();
 int assemble_long_row_ctas();
 
 namespace {
@@ -41,6 +42,7 @@ void carve_all(agipc_ctx *c, char *base, size_t *total)
     c->fine_brow = cv.take<int32_t>((size_t)c->max_fine_nnzb);
     c->long_rows = cv.take<int32_t>(n + 1);
     c->bitmap = cv.take<uint32_t>((size_t)assemble_long_row_ctas() * (size_t)c->bitmap_words);
+    c->dinv64 = cv.take<double>(9 * n);
     c->pcg.r = cv.take<double>(3 * n);
     c->pcg.u = cv.take<double>(3 * n);
     c->pcg.w = cv.take<double>(3 * n);
@@ -102,6 +104,15 @@ extern "C" int agipc_create(agipc_ctx **out, void *cuda_stream, int32_t max_fine
     // Persistent PCG: as many co-resident CTAs as the occupancy allows, capped
     // at two per SM (the grid barrier's cost grows with the CTA count).
     int per_sm = 0;
+    int per_sm_mixed = 0;
+    if (cudaFuncSetAttribute(pcg_mixed_kernel_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, pcg_smem_bytes()) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_mixed, pcg_mixed_kernel_ptr(), pcg_block_size(),
+                                                      pcg_smem_bytes()) != cudaSuccess ||
+        per_sm_mixed < 1) {
+        delete c;
+        return AGIPC_ERR_CUDA;
+    }
     if (cudaFuncSetAttribute(pcg_kernel_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, pcg_smem_bytes()) !=
             cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_kernel_ptr(), pcg_block_size(), pcg_smem_bytes()) !=
@@ -113,7 +124,7 @@ extern "C" int agipc_create(agipc_ctx **out, void *cuda_stream, int32_t max_fine
     int cap_per_sm = 2;
     if (const char *env = std::getenv("AGIPC_PCG_CTAS_PER_SM")) cap_per_sm = std::max(1, std::atoi(env));
     c->pcg_block = pcg_block_size();
-    c->pcg_grid = std::min(per_sm, cap_per_sm) * c->num_sms;
+    c->pcg_grid = std::min(std::min(per_sm, per_sm_mixed), cap_per_sm) * c->num_sms;
     c->pcg.max_grid = c->pcg_grid;
 
     size_t bytes = 0;

@@ -52,6 +52,9 @@ __device__ __forceinline__ int64_t slot_of(unsigned long long key, int bits)
     return (int64_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - bits));
 }
 
+// Sources of terms: fine upper blocks (FP64 or FP32), barrier stencils
+// (FP64 or FP32) and, for the precision form, a second list of stencils kept
+// in FP64 (small gaps).  Term t indexes them in that order.
 struct TermArgs {
     int32_t n;
     const int32_t *labels;
@@ -59,37 +62,81 @@ struct TermArgs {
     const int32_t *fine_brow;
     const int32_t *fine_col;
     const double *fine_val;
+    const float *fine_val32;  // used when fine_val is null
     int64_t fine_nnzb;
     const int32_t *pair_idx;
     const double *pair_blk;
+    const float *pair_blk32;  // used when pair_blk is null
+    int64_t n_pairs;
+    const int32_t *pair_idx2;
+    const double *pair_blk2;
+    int64_t n_pairs2;
     int64_t n_terms;
 };
 
 // Coarse (row label, column label) of term t and whether its source block is
-// off-diagonal; false when an index is out of range.
+// off-diagonal; false when an index is out of range.  `src` is the offset of
+// the term's 9 values in its array and `kind` which array: 0 fine FP64,
+// 1 fine FP32, 2 stencil FP64, 3 stencil FP32, 4 second stencil list (FP64).
 __device__ __forceinline__ bool term_labels(const TermArgs &A, int64_t t, int32_t nc, int32_t &a, int32_t &b,
-                                            bool &offdiag, const double *&blk)
+                                            bool &offdiag, int64_t &src, int &kind)
 {
     int32_t vi, vj;
     if (t < A.fine_nnzb) {
         vi = A.fine_brow[t];
         vj = A.fine_col[t];
         offdiag = vi != vj;
-        blk = A.fine_val + 9 * t;
+        src = 9 * t;
+        kind = A.fine_val ? 0 : 1;
         if ((unsigned)vi >= (unsigned)A.n || (unsigned)vj >= (unsigned)A.n || vj < vi) return false;
     } else {
-        const int64_t u = t - A.fine_nnzb;
+        int64_t u = t - A.fine_nnzb;
+        const int32_t *idx;
+        if (u < 10 * A.n_pairs) {
+            idx = A.pair_idx;
+            kind = A.pair_blk ? 2 : 3;
+        } else {
+            u -= 10 * A.n_pairs;
+            idx = A.pair_idx2;
+            kind = 4;
+        }
         const int64_t p = u / 10;
         const int q = (int)(u - 10 * p);
-        vi = A.pair_idx[4 * p + c_stencil_s[q]];
-        vj = A.pair_idx[4 * p + c_stencil_t[q]];
+        vi = idx[4 * p + c_stencil_s[q]];
+        vj = idx[4 * p + c_stencil_t[q]];
         offdiag = c_stencil_s[q] != c_stencil_t[q];
-        blk = A.pair_blk + 90 * p + 9 * q;
+        src = 90 * p + 9 * q;
         if ((unsigned)vi >= (unsigned)A.n || (unsigned)vj >= (unsigned)A.n) return false;
     }
     a = A.labels[vi];
     b = A.labels[vj];
     return (unsigned)a < (unsigned)nc && (unsigned)b < (unsigned)nc;
+}
+
+__device__ __forceinline__ void load_term(const TermArgs &A, int64_t src, int kind, double B[9])
+{
+    switch (kind) {
+    case 0:
+#pragma unroll
+        for (int e = 0; e < 9; ++e) B[e] = __ldg(A.fine_val + src + e);
+        break;
+    case 1:
+#pragma unroll
+        for (int e = 0; e < 9; ++e) B[e] = (double)__ldg(A.fine_val32 + src + e);
+        break;
+    case 2:
+#pragma unroll
+        for (int e = 0; e < 9; ++e) B[e] = __ldg(A.pair_blk + src + e);
+        break;
+    case 3:
+#pragma unroll
+        for (int e = 0; e < 9; ++e) B[e] = (double)__ldg(A.pair_blk32 + src + e);
+        break;
+    default:
+#pragma unroll
+        for (int e = 0; e < 9; ++e) B[e] = __ldg(A.pair_blk2 + src + e);
+        break;
+    }
 }
 
 __global__ void fine_rows_kernel(int32_t n, const int32_t *__restrict__ rp, int64_t nnzb, int32_t *__restrict__ brow,
@@ -135,8 +182,9 @@ __global__ void symbolic_kernel(TermArgs A, unsigned long long *keys, int bits, 
         int32_t a = 0, b = 0;
         if (t < A.n_terms) {
             bool off;
-            const double *blk;
-            if (term_labels(A, t, nc, a, b, off, blk))
+            int64_t src;
+            int kind;
+            if (term_labels(A, t, nc, a, b, off, src, kind))
                 key = pack_key(min(a, b), max(a, b));
             else
                 set_status(status, ST_BAD_INDEX);
@@ -317,11 +365,11 @@ __device__ __forceinline__ bool term_value(const TermArgs &A, int64_t t, int32_t
 {
     int32_t a, b;
     bool off;
-    const double *blk;
-    if (!term_labels(A, t, nc, a, b, off, blk)) return false;
+    int64_t src;
+    int kind;
+    if (!term_labels(A, t, nc, a, b, off, src, kind)) return false;
     double B[9];
-#pragma unroll
-    for (int e = 0; e < 9; ++e) B[e] = __ldg(blk + e);
+    load_term(A, src, kind, B);
     if (a == b) {
 #pragma unroll
         for (int r = 0; r < 3; ++r)
@@ -529,25 +577,26 @@ __global__ void gradient_kernel(int32_t n, const int32_t *__restrict__ labels, c
     }
 }
 
+__global__ void to_fp32_kernel(const int32_t *__restrict__ n_c_dev, const int32_t *__restrict__ nnz_dev, int64_t cap,
+                               const double *__restrict__ val, float *__restrict__ val32,
+                               const double *__restrict__ dinv, float *__restrict__ dinv32)
+{
+    const int64_t nnz = min64((int64_t)*nnz_dev, cap);
+    const int64_t nc = *n_c_dev;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < 9 * nnz; k += stride) val32[k] = (float)val[k];
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < 9 * nc; k += stride) dinv32[k] = (float)dinv[k];
+}
+
 }  // namespace
 
-extern "C" int agipc_assemble_coarse(agipc_ctx *ctx, int32_t n_fine, const int32_t *labels, const int32_t *n_coarse_dev,
-                                     const int32_t *fine_row_ptr, const int32_t *fine_col, const double *fine_val,
-                                     int64_t fine_nnzb, int64_t n_pairs, const int32_t *pair_idx,
-                                     const double *pair_blk, const double *g, int32_t *coarse_row_ptr,
-                                     int32_t *coarse_col, double *coarse_val, int64_t coarse_cap_nnzb,
-                                     int32_t *coarse_nnzb_dev, double *g_c, double *dinv)
+static int assemble_impl(agipc_ctx *ctx, int32_t n_fine, const int32_t *fine_row_ptr, TermArgs &A,
+                         const double *g, int32_t *coarse_row_ptr, int32_t *coarse_col, double *coarse_val,
+                         int64_t coarse_cap_nnzb, int32_t *coarse_nnzb_dev, double *g_c, double *dinv)
 {
-    if (!ctx || n_fine <= 0 || n_fine > ctx->max_n || fine_nnzb < 0 || fine_nnzb > ctx->max_fine_nnzb || n_pairs < 0 ||
-        n_pairs > ctx->max_pairs || coarse_cap_nnzb < 0)
-        return AGIPC_ERR_INVALID_ARG;
-    if (!labels || !n_coarse_dev || !fine_row_ptr || (fine_nnzb > 0 && (!fine_col || !fine_val)) ||
-        (n_pairs > 0 && (!pair_idx || !pair_blk)) || !g || !coarse_row_ptr || !coarse_nnzb_dev || !g_c || !dinv ||
-        (coarse_cap_nnzb > 0 && (!coarse_col || !coarse_val)))
-        return AGIPC_ERR_INVALID_ARG;
-    if (coarse_cap_nnzb > INT32_MAX) return AGIPC_ERR_INVALID_ARG;
     cudaStream_t st = ctx->stream;
-    const int64_t n_terms = fine_nnzb + 10 * n_pairs;
+    const int64_t n_terms = A.n_terms;
+    const int32_t *n_coarse_dev = A.n_c_dev;
     int bits = 10;
     while ((1ll << bits) < n_terms + n_terms / 4 && bits < ctx->hbits) ++bits;
     const int64_t nslots = 1ll << bits;
@@ -558,20 +607,8 @@ extern "C" int agipc_assemble_coarse(agipc_ctx *ctx, int32_t n_fine, const int32
         cudaMemsetAsync(ctx->long_rows + ctx->max_n, 0, sizeof(int32_t), st) != cudaSuccess)
         return AGIPC_ERR_CUDA;
 
-    TermArgs A;
-    A.n = n_fine;
-    A.labels = labels;
-    A.n_c_dev = n_coarse_dev;
-    A.fine_brow = ctx->fine_brow;
-    A.fine_col = fine_col;
-    A.fine_val = fine_val;
-    A.fine_nnzb = fine_nnzb;
-    A.pair_idx = pair_idx;
-    A.pair_blk = pair_blk;
-    A.n_terms = n_terms;
-
     const unsigned grid_sm = (unsigned)ctx->num_sms * 8;
-    fine_rows_kernel<<<(unsigned)div_up(n_fine, kTb), kTb, 0, st>>>(n_fine, fine_row_ptr, fine_nnzb, ctx->fine_brow,
+    fine_rows_kernel<<<(unsigned)div_up(n_fine, kTb), kTb, 0, st>>>(n_fine, fine_row_ptr, A.fine_nnzb, ctx->fine_brow,
                                                                     ctx->status);
     const unsigned gt = (unsigned)std::min<int64_t>(div_up(n_terms > 0 ? n_terms : 1, kTb), (int64_t)grid_sm * 4);
     symbolic_kernel<<<gt, kTb, 0, st>>>(A, ctx->hkeys, bits, ctx->row_cnt, ctx->status);
@@ -594,7 +631,80 @@ extern "C" int agipc_assemble_coarse(agipc_ctx *ctx, int32_t n_fine, const int32
     dinv_kernel<<<(unsigned)std::min<int64_t>(div_up(n_fine, kTb), (int64_t)grid_sm * 4), kTb, 0, st>>>(
         n_coarse_dev, coarse_row_ptr, coarse_col, coarse_cap_nnzb, coarse_val, dinv, ctx->status);
     gradient_kernel<<<(unsigned)std::min<int64_t>(div_up(n_fine, kTb), (int64_t)grid_sm * 4), kTb, 0, st>>>(
-        n_fine, labels, n_coarse_dev, g, g_c, ctx->status);
+        n_fine, A.labels, n_coarse_dev, g, g_c, ctx->status);
+    return cudaPeekAtLastError() == cudaSuccess ? AGIPC_OK : AGIPC_ERR_CUDA;
+}
+
+extern "C" int agipc_assemble_coarse(agipc_ctx *ctx, int32_t n_fine, const int32_t *labels, const int32_t *n_coarse_dev,
+                                     const int32_t *fine_row_ptr, const int32_t *fine_col, const double *fine_val,
+                                     int64_t fine_nnzb, int64_t n_pairs, const int32_t *pair_idx,
+                                     const double *pair_blk, const double *g, int32_t *coarse_row_ptr,
+                                     int32_t *coarse_col, double *coarse_val, int64_t coarse_cap_nnzb,
+                                     int32_t *coarse_nnzb_dev, double *g_c, double *dinv)
+{
+    if (!ctx || n_fine <= 0 || n_fine > ctx->max_n || fine_nnzb < 0 || fine_nnzb > ctx->max_fine_nnzb || n_pairs < 0 ||
+        n_pairs > ctx->max_pairs || coarse_cap_nnzb < 0)
+        return AGIPC_ERR_INVALID_ARG;
+    if (!labels || !n_coarse_dev || !fine_row_ptr || (fine_nnzb > 0 && (!fine_col || !fine_val)) ||
+        (n_pairs > 0 && (!pair_idx || !pair_blk)) || !g || !coarse_row_ptr || !coarse_nnzb_dev || !g_c || !dinv ||
+        (coarse_cap_nnzb > 0 && (!coarse_col || !coarse_val)))
+        return AGIPC_ERR_INVALID_ARG;
+    if (coarse_cap_nnzb > INT32_MAX) return AGIPC_ERR_INVALID_ARG;
+    TermArgs A = {};
+    A.n = n_fine;
+    A.labels = labels;
+    A.n_c_dev = n_coarse_dev;
+    A.fine_brow = ctx->fine_brow;
+    A.fine_col = fine_col;
+    A.fine_val = fine_val;
+    A.fine_nnzb = fine_nnzb;
+    A.pair_idx = pair_idx;
+    A.pair_blk = pair_blk;
+    A.n_pairs = n_pairs;
+    A.n_terms = fine_nnzb + 10 * n_pairs;
+    return assemble_impl(ctx, n_fine, fine_row_ptr, A, g, coarse_row_ptr, coarse_col, coarse_val, coarse_cap_nnzb,
+                         coarse_nnzb_dev, g_c, dinv);
+}
+
+extern "C" int agipc_assemble_coarse_mixed(agipc_ctx *ctx, int32_t n_fine, const int32_t *labels,
+                                           const int32_t *n_coarse_dev, const int32_t *fine_row_ptr,
+                                           const int32_t *fine_col, const float *fine_val32, int64_t fine_nnzb,
+                                           int64_t n_pairs32, const int32_t *pair_idx32, const float *pair_blk32,
+                                           int64_t n_pairs64, const int32_t *pair_idx64, const double *pair_blk64,
+                                           const double *g, int32_t *coarse_row_ptr, int32_t *coarse_col,
+                                           double *coarse_val, float *coarse_val32, int64_t coarse_cap_nnzb,
+                                           int32_t *coarse_nnzb_dev, double *g_c, float *dinv32)
+{
+    if (!ctx || n_fine <= 0 || n_fine > ctx->max_n || fine_nnzb < 0 || fine_nnzb > ctx->max_fine_nnzb ||
+        n_pairs32 < 0 || n_pairs64 < 0 || n_pairs32 + n_pairs64 > ctx->max_pairs || coarse_cap_nnzb < 0)
+        return AGIPC_ERR_INVALID_ARG;
+    if (!labels || !n_coarse_dev || !fine_row_ptr || (fine_nnzb > 0 && (!fine_col || !fine_val32)) ||
+        (n_pairs32 > 0 && (!pair_idx32 || !pair_blk32)) || (n_pairs64 > 0 && (!pair_idx64 || !pair_blk64)) || !g ||
+        !coarse_row_ptr || !coarse_nnzb_dev || !g_c || !dinv32 ||
+        (coarse_cap_nnzb > 0 && (!coarse_col || !coarse_val || !coarse_val32)))
+        return AGIPC_ERR_INVALID_ARG;
+    if (coarse_cap_nnzb > INT32_MAX) return AGIPC_ERR_INVALID_ARG;
+    TermArgs A = {};
+    A.n = n_fine;
+    A.labels = labels;
+    A.n_c_dev = n_coarse_dev;
+    A.fine_brow = ctx->fine_brow;
+    A.fine_col = fine_col;
+    A.fine_val32 = fine_val32;
+    A.fine_nnzb = fine_nnzb;
+    A.pair_idx = pair_idx32;
+    A.pair_blk32 = pair_blk32;
+    A.n_pairs = n_pairs32;
+    A.pair_idx2 = pair_idx64;
+    A.pair_blk2 = pair_blk64;
+    A.n_pairs2 = n_pairs64;
+    A.n_terms = fine_nnzb + 10 * (n_pairs32 + n_pairs64);
+    int rc = assemble_impl(ctx, n_fine, fine_row_ptr, A, g, coarse_row_ptr, coarse_col, coarse_val, coarse_cap_nnzb,
+                           coarse_nnzb_dev, g_c, ctx->dinv64);
+    if (rc != AGIPC_OK) return rc;
+    const unsigned grid = (unsigned)ctx->num_sms * 8;
+    to_fp32_kernel<<<grid, kTb, 0, ctx->stream>>>(n_coarse_dev, coarse_nnzb_dev, coarse_cap_nnzb, coarse_val,
+                                                   coarse_val32, ctx->dinv64, dinv32);
     return cudaPeekAtLastError() == cudaSuccess ? AGIPC_OK : AGIPC_ERR_CUDA;
 }
 

@@ -40,21 +40,11 @@
 #include <algorithm>
 
 #include "agipc_common.cuh"
+#include "pcg_slices.cuh"
+
+using namespace pcgs;
 
 namespace {
-
-constexpr int kPcgBlock = 256;
-constexpr int kPcgWarps = kPcgBlock / 32;
-constexpr int kK = 5;                          // consecutive blocks per lane
-constexpr int kSlice = 32 * kK;                // blocks per warp slice
-constexpr int kValBytes = kSlice * 9 * 8;      // 11520
-constexpr int kIdxBytes = kSlice * 4;          // 640 per index array
-constexpr int kBufBytes = kValBytes + 2 * kIdxBytes;
-constexpr int kJoinBytes = 32 * (3 * 8 + 3 * 4);
-constexpr int kWarpSmem = 2 * kBufBytes + kJoinBytes;
-constexpr int kPartBytes = kPcgBlock * 3 * 8;
-constexpr int kPcgSmem = kPcgWarps * kWarpSmem + kPartBytes;
-constexpr int kMaxGridLanes = 8;               // the grid reduction handles up to 256 CTAs
 
 struct PcgArgs {
     const int32_t *n_dev;
@@ -74,190 +64,6 @@ struct PcgArgs {
     PcgScratch S;
     uint32_t *status;
 };
-
-__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src, int src_bytes)
-{
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gmem_src), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-// Copy slice `sl` (values, columns, rows) into a warp buffer; zero-fills
-// past the last block so no byte beyond the arrays is read.
-__device__ __forceinline__ void issue_slice(unsigned char *buf, int64_t sl, int64_t nnz, const double *val,
-                                            const int32_t *col, const int32_t *brow, int lane)
-{
-    const int64_t base = sl * kSlice;
-    const int cnt = (int)min64(kSlice, nnz - base);
-    const int vbytes = 72 * cnt, ibytes = 4 * cnt;
-    const unsigned char *vs = reinterpret_cast<const unsigned char *>(val + 9 * base);
-    const unsigned char *cs = reinterpret_cast<const unsigned char *>(col + base);
-    const unsigned char *rs = reinterpret_cast<const unsigned char *>(brow + base);
-    for (int q = lane; 16 * q < vbytes; q += 32) cp_async16(buf + 16 * q, vs + 16 * q, min(16, vbytes - 16 * q));
-    for (int q = lane; 16 * q < ibytes; q += 32) {
-        cp_async16(buf + kValBytes + 16 * q, cs + 16 * q, min(16, ibytes - 16 * q));
-        cp_async16(buf + kValBytes + kIdxBytes + 16 * q, rs + 16 * q, min(16, ibytes - 16 * q));
-    }
-}
-
-// Sum of N values per thread over the CTA: threads park their values in
-// shared memory, warp 0 adds them with a tree (3 levels over the 8 warps,
-// then 5 shuffle levels).  The result is valid in thread 0.
-template <int N>
-__device__ __forceinline__ void cta_sum(double (&v)[N], double *s_part, double *s_out)
-{
-    // Warp k adds value k (each warp sits on its own SM sub-partition, whose
-    // FP64 pipe is the bottleneck): 3 tree levels over the 8 warps' slots,
-    // then 5 shuffle levels.  Totals land in s_out[0..N) for every thread.
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < N; ++k) s_part[N * threadIdx.x + k] = v[k];
-    __syncthreads();
-    if (wid < N) {
-        double t[kPcgWarps];
-#pragma unroll
-        for (int q = 0; q < kPcgWarps; ++q) t[q] = s_part[N * (lane + 32 * q) + wid];
-#pragma unroll
-        for (int h = kPcgWarps / 2; h > 0; h >>= 1)
-#pragma unroll
-            for (int q = 0; q < h; ++q) t[q] += t[q + h];
-        const double tot = warp_sum(t[0]);
-        if (lane == 0) s_out[wid] = tot;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < N; ++k) v[k] = s_out[k];
-}
-
-__device__ __forceinline__ void store_row(double *w, int row, bool split, const double y[3])
-{
-    double *dst = w + 3 * (int64_t)row;
-    if (split) {
-        atomicAdd(dst, y[0]);
-        atomicAdd(dst + 1, y[1]);
-        atomicAdd(dst + 2, y[2]);
-    } else {
-        dst[0] = y[0];
-        dst[1] = y[1];
-        dst[2] = y[2];
-    }
-}
-
-__device__ __forceinline__ double dsel(bool c, double a, double b)
-{
-    // select on the bit pattern: integer moves, no FP64 instruction
-    return __longlong_as_double(c ? __double_as_longlong(a) : __double_as_longlong(b));
-}
-
-// w = A u over one slice held in `buf` (rows inside the slice) or += (rows
-// cut by its ends); adds this lane's share of delta to dpart.
-//
-// Per lane the 5 blocks are folded left to right into one running row
-// accumulator (reset at a row change by a select, so the FP64 work is
-// exactly 9 FMAs per block with no divergence); a row segment's total is the
-// accumulator at the segment's last block.  delta takes u_row . total at
-// each segment end.  Segments that cross lanes are joined by the lane where
-// the row starts, which walks forward over the lanes that continue it.
-__device__ __forceinline__ void slice_spmv(const unsigned char *buf, int cnt, const double *u, double *w,
-                                           const uint8_t *rowflag, unsigned char *join, int lane, double &dpart)
-{
-    const double *s_val = reinterpret_cast<const double *>(buf);
-    const int32_t *s_col = reinterpret_cast<const int32_t *>(buf + kValBytes);
-    const int32_t *s_row = reinterpret_cast<const int32_t *>(buf + kValBytes + kIdxBytes);
-    int rows_[kK];
-    double xv[kK][3];
-    double ur[kK][3];
-    bool split[kK];
-#pragma unroll
-    for (int j = 0; j < kK; ++j) {
-        const int q = lane * kK + j;
-        rows_[j] = -1;
-        split[j] = false;
-        xv[j][0] = xv[j][1] = xv[j][2] = 0.0;
-        ur[j][0] = ur[j][1] = ur[j][2] = 0.0;
-        if (q < cnt) {
-            const int rj = s_row[q];
-            rows_[j] = rj;
-            const double *uc = u + 3 * (int64_t)s_col[q];
-            xv[j][0] = __ldcg(uc);
-            xv[j][1] = __ldcg(uc + 1);
-            xv[j][2] = __ldcg(uc + 2);
-            if (j == 0 || rj != s_row[q - 1]) {  // first block of a row segment
-                const double *up = u + 3 * (int64_t)rj;
-                ur[j][0] = __ldcg(up);
-                ur[j][1] = __ldcg(up + 1);
-                ur[j][2] = __ldcg(up + 2);
-                split[j] = (__ldcg(rowflag + rj) & 1) != 0;
-            }
-        }
-    }
-    // running accumulator; segment bookkeeping by selects
-    double acc[3] = {0.0, 0.0, 0.0};
-    double fa[3] = {0.0, 0.0, 0.0}, la[3] = {0.0, 0.0, 0.0};
-    int fr = -1, lr = -1;
-    bool f_split = false, l_split = false, s_cur = false, first_open = true;
-    double cu[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-    for (int j = 0; j < kK; ++j) {
-        const bool valid = rows_[j] >= 0;
-        const bool start = valid && (j == 0 || rows_[j] != rows_[j - 1]);
-        const bool end = valid && (j == kK - 1 || rows_[j + 1] != rows_[j]);
-        const double *B = s_val + 9 * (lane * kK + j);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            cu[c] = dsel(start, ur[j][c], cu[c]);
-            acc[c] = dsel(start, 0.0, acc[c]);
-            acc[c] = fma(B[3 * c + 2], xv[j][2], fma(B[3 * c + 1], xv[j][1], fma(B[3 * c], xv[j][0], acc[c])));
-        }
-        s_cur = start ? split[j] : s_cur;
-        // delta: u_row . segment total at every segment end (zero elsewhere)
-        dpart = fma(dsel(end, cu[0], 0.0), acc[0], fma(dsel(end, cu[1], 0.0), acc[1], fma(dsel(end, cu[2], 0.0), acc[2], dpart)));
-        if (end) {
-            const bool last = j == kK - 1 || rows_[j + 1] < 0;
-            if (first_open) {                       // the lane's first segment: joined below
-                fr = rows_[j]; f_split = s_cur;
-                fa[0] = acc[0]; fa[1] = acc[1]; fa[2] = acc[2];
-                first_open = false;
-            } else if (last) {                      // the lane's last segment: joined below
-                lr = rows_[j]; l_split = s_cur;
-                la[0] = acc[0]; la[1] = acc[1]; la[2] = acc[2];
-            } else {                                // a row wholly inside this lane
-                store_row(w, rows_[j], s_cur, acc);
-            }
-        }
-    }
-    const bool single = lr < 0;
-    double *s_fa = reinterpret_cast<double *>(join);
-    int32_t *s_fr = reinterpret_cast<int32_t *>(join + 32 * 24);
-    int32_t *s_single = s_fr + 32;
-    int32_t *s_last = s_fr + 64;
-    s_fr[lane] = fr;
-    s_single[lane] = single ? 1 : 0;
-    s_last[lane] = single ? fr : lr;
-    s_fa[3 * lane] = fa[0];
-    s_fa[3 * lane + 1] = fa[1];
-    s_fa[3 * lane + 2] = fa[2];
-    __syncwarp();
-    if (!single) {
-        for (int q = lane + 1; q < 32 && s_fr[q] == lr; ++q) {
-            la[0] += s_fa[3 * q]; la[1] += s_fa[3 * q + 1]; la[2] += s_fa[3 * q + 2];
-            if (!s_single[q]) break;
-        }
-        store_row(w, lr, l_split, la);
-    }
-    if (fr >= 0 && (lane == 0 || s_last[lane - 1] != fr)) {
-        if (single) {
-            for (int q = lane + 1; q < 32 && s_fr[q] == fr; ++q) {
-                fa[0] += s_fa[3 * q]; fa[1] += s_fa[3 * q + 1]; fa[2] += s_fa[3 * q + 2];
-                if (!s_single[q]) break;
-            }
-        }
-        store_row(w, fr, f_split, fa);
-    }
-    __syncwarp();
-}
 
 // Row-local update of one row i: p = u + beta p, s = w + beta s,
 // x += alpha p, r -= alpha s, u = M^-1 r; returns gamma, rho shares.
@@ -413,7 +219,7 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_kernel(PcgArgs A)
             }
             __syncwarp();
             const int cnt = (int)min64(kSlice, nnz - sl * kSlice);
-            slice_spmv(wbuf + nb * kBufBytes, cnt, u, w, rowflag, join, lane, dpart);
+            slice_spmv<double, true>(wbuf + nb * kBufBytes, cnt, u, w, rowflag, join, lane, dpart);
             if (!resident) nb ^= 1;
         }
         // one row per thread: fetch the row's own state now, so that only w

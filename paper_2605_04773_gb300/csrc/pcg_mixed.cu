@@ -1,0 +1,404 @@
+// Mixed-precision block-Jacobi PCG: the precision form of the coarse solve.
+//
+// The 3x3 blocks, the SpMV and the block-Jacobi preconditioner run in FP32;
+// the dot products (gamma = r.u, rho = r.r, delta = u.Au) are accumulated in
+// FP64; x and r are kept in FP64, and every `refine_every` iterations r is
+// replaced by the true residual b - A x computed with the FP64 master matrix
+// (residual replacement), so the iteration converges to the FP64 system's
+// solution while nearly all of its arithmetic runs on the FP32 units, which
+// on GB300 are ~56x faster than the FP64 ones.
+//
+// Same structure as the FP64 kernel (pcg.cu): one persistent cooperative
+// launch, Chronopoulos-Gear recurrence, FP32 slices of 160 blocks staged by
+// cp.async and resident in shared memory when they fit.  A refinement
+// iteration adds an FP64 slice SpMV of x (staged in the warp's free buffer)
+// and one grid barrier.
+#include <algorithm>
+
+#include "agipc_common.cuh"
+#include "pcg_slices.cuh"
+
+using namespace pcgs;
+
+namespace {
+
+struct MixedArgs {
+    const int32_t *n_dev;
+    const int32_t *rp;
+    const int32_t *col;
+    const double *val64;
+    const float *val32;
+    const float *dinv32;
+    const double *b;
+    double *x;
+    double sign;
+    double tol;
+    int32_t max_iter;
+    int32_t refine_every;
+    int32_t max_rows;
+    int64_t max_nnzb;
+    int32_t *iters_dev;
+    double *relres_dev;
+    PcgScratch S;
+    uint32_t *status;
+};
+
+__device__ __forceinline__ void precond32(const float *D, const double r[3], float u[3])
+{
+    const float r0 = (float)r[0], r1 = (float)r[1], r2 = (float)r[2];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) u[c] = fmaf(D[3 * c + 2], r2, fmaf(D[3 * c + 1], r1, D[3 * c] * r0));
+}
+
+__global__ void __launch_bounds__(kPcgBlock, 1) pcg_mixed_kernel(MixedArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double s_scal[2];
+    __shared__ double s_tot[4];
+    __shared__ double s_grid[3];
+    __shared__ int s_dec;
+    __shared__ bool s_ref;
+
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const unsigned nblocks = gridDim.x;
+    const int64_t nwarps = (int64_t)nblocks * kPcgWarps;
+    const int64_t gwarp = (int64_t)wib * nblocks + blockIdx.x;
+    const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+
+    const int32_t n = *A.n_dev;
+    if (n < 0 || n > A.max_rows || nblocks > 32 * kMaxGridLanes) {
+        if (gtid == 0) set_status(A.status, ST_BAD_INDEX);
+        return;
+    }
+    const int64_t nnz = A.rp[n];
+    if (nnz < 0 || nnz > A.max_nnzb) {
+        if (gtid == 0) set_status(A.status, nnz < 0 ? ST_BAD_INDEX : ST_CAPACITY);
+        return;
+    }
+    const int64_t nslices = div_up(nnz, kSlice);
+    const bool resident = nslices <= nwarps;
+    const int64_t rows_per_cta = div_up(n, nblocks);
+    const int64_t row0 = min64((int64_t)blockIdx.x * rows_per_cta, n);
+    const int64_t row1 = min64(row0 + rows_per_cta, n);
+
+    // vectors: r, ax in FP64; u, w, p, s in FP32 (two FP32 vectors share one
+    // FP64-sized scratch array)
+    double *__restrict__ r = A.S.r;
+    double *ax = A.S.u;
+    float *w = reinterpret_cast<float *>(A.S.w);
+    float *u = w + 3 * (int64_t)A.max_rows;
+    float *__restrict__ p = reinterpret_cast<float *>(A.S.p);
+    float *__restrict__ s = reinterpret_cast<float *>(A.S.s);
+    double *__restrict__ x = A.x;
+    int32_t *brow = A.S.brow;
+    uint8_t *rowflag = A.S.rowflag;
+    double *partials = A.S.partials;
+    unsigned *count = A.S.bar;
+    const int pstride = A.S.max_grid * 4;
+    unsigned epoch = 0;
+    unsigned char *wbuf = smem + (size_t)wib * kWarpSmem;
+    unsigned char *join = wbuf + 2 * kBufBytes;
+    double *s_part = reinterpret_cast<double *>(smem + (size_t)kPcgWarps * kWarpSmem);
+
+    // ---- setup
+    double gpart = 0.0, rpart = 0.0;
+    for (int64_t i = row0 + threadIdx.x; i < row1; i += blockDim.x) {
+        const int32_t k0 = A.rp[i], k1 = A.rp[i + 1];
+        bool bad = k0 < 0 || k1 < k0 || k1 > nnz;
+        for (int32_t k = k0; !bad && k < k1; ++k) {
+            brow[k] = (int32_t)i;
+            bad = (unsigned)A.col[k] >= (unsigned)n;
+        }
+        if (bad) atomicOr(A.S.bar + 32, 1u);
+        uint8_t f = 0;
+        if (k1 == k0) f = 2;
+        else if (k0 / kSlice != (k1 - 1) / kSlice) f = 1;
+        rowflag[i] = f;
+        double rr[3];
+        float uu[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            rr[c] = A.sign * A.b[3 * i + c];
+            x[3 * i + c] = 0.0;
+            p[3 * i + c] = 0.0f;
+            s[3 * i + c] = 0.0f;
+            w[3 * i + c] = 0.0f;
+            r[3 * i + c] = rr[c];
+        }
+        precond32(A.dinv32 + 9 * i, rr, uu);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            u[3 * i + c] = uu[c];
+            gpart = fma(rr[c], (double)uu[c], gpart);
+            rpart = fma(rr[c], rr[c], rpart);
+        }
+    }
+    {
+        double v[2] = {gpart, rpart};
+        cta_sum<2>(v, s_part, s_tot);
+        if (threadIdx.x == 0) {
+            partials[blockIdx.x * 4 + 0] = v[0];
+            partials[blockIdx.x * 4 + 1] = v[1];
+        }
+    }
+    bool ok = grid_sync(count, nblocks, epoch, A.status);
+    if (ok && ld_acquire_u32(A.S.bar + 32) != 0u) {
+        if (gtid == 0) set_status(A.status, ST_BAD_INDEX);
+        ok = false;
+    }
+    int nb = 0;
+    if (ok && gwarp < nslices) issue_slice(wbuf, gwarp, nnz, A.val32, A.col, brow, lane);
+    cp_async_commit();
+
+    double alpha_old = 1.0, gamma_old = 1.0, bnorm2 = 0.0, rnorm2 = 0.0;
+    const double tol2 = A.tol * A.tol;
+    bool fresh = true;  // the residual was just computed as b - A64 x (x = 0 at the start)
+    bool tight = false, last_verify = false, restart = false;
+    int32_t it = 0;
+    bool converged = false;
+    while (ok) {
+        const int par = it & 1;
+        double *part = partials + par * pstride;
+        // ---- S phase: w = A32 u (FP32), delta accumulated in FP64 per lane
+        double dpart = 0.0;
+        for (int64_t sl = gwarp; sl < nslices; sl += nwarps) {
+            if (!resident) {
+                const int64_t next = sl + nwarps < nslices ? sl + nwarps : gwarp;
+                issue_slice(wbuf + (nb ^ 1) * kBufBytes, next, nnz, A.val32, A.col, brow, lane);
+                cp_async_commit();
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncwarp();
+            const int cnt = (int)min64(kSlice, nnz - sl * kSlice);
+            slice_spmv<float, true>(wbuf + nb * kBufBytes, cnt, u, w, rowflag, join, lane, dpart);
+            if (!resident) nb ^= 1;
+        }
+        {
+            double v[1] = {dpart};
+            cta_sum<1>(v, s_part, s_tot);
+            if (threadIdx.x == 0) part[blockIdx.x * 4 + 2] = v[0];
+        }
+        if (!grid_sync(count, nblocks, epoch, A.status)) { ok = false; break; }
+
+        // ---- global scalars (as in the FP64 kernel)
+        if (wib < 3) {
+            double pv[kMaxGridLanes];
+#pragma unroll
+            for (int q = 0; q < kMaxGridLanes; ++q) {
+                const unsigned k = lane + 32 * q;
+                pv[q] = k < nblocks ? __ldcg(part + k * 4 + wib) : 0.0;
+            }
+#pragma unroll
+            for (int h = kMaxGridLanes / 2; h > 0; h >>= 1)
+#pragma unroll
+                for (int q = 0; q < h; ++q) pv[q] += pv[q + h];
+            const double tot = warp_sum(pv[0]);
+            if (lane == 0) s_grid[wib] = tot;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const double g = s_grid[0], rh = s_grid[1], dl = s_grid[2];
+            // 0 iterate, 1 converged, 2 iteration cap, 3 non-finite, 4 verify:
+            // the recurrence residual met the tolerance but was not freshly
+            // recomputed, so replace it by b - A64 x before stopping
+            int decision = 0;
+            double alpha = 0.0, beta = 0.0;
+            rnorm2 = rh;
+            if (it == 0) bnorm2 = rh;
+            if (!isfinite(rh) || !isfinite(g) || !isfinite(dl)) decision = 3;
+            else if (bnorm2 == 0.0 || rh <= tol2 * bnorm2) decision = (fresh || A.refine_every == 0) ? 1 : 4;
+            else if (it >= A.max_iter) decision = 2;
+            // A verify that did not confirm convergence: the FP32 recurrences
+            // of r and s = A p have drifted.  Restart the recurrence once
+            // (beta = 0: p = u, s = w = A u from the fresh residual) and from
+            // then on replace the residual every iteration.
+            if (last_verify && decision != 1 && !tight) {
+                tight = true;
+                restart = true;
+            }
+            if (decision == 0 || decision == 4) {
+                s_ref = decision == 4 || tight ||
+                        (A.refine_every > 0 && ((it + 1) % A.refine_every) == 0);
+                fresh = s_ref;
+                last_verify = decision == 4;
+            }
+            if (decision != 0) {
+                // no Krylov step this time
+            } else {
+                if (it == 0 || restart) {
+                    alpha = g / dl;
+                    restart = false;
+                } else {
+                    const double t = gamma_old * alpha_old;
+                    beta = g / gamma_old;
+                    alpha = (g * t) / fma(dl, t, -g * g);
+                }
+                if (!isfinite(alpha) || !isfinite(beta)) decision = 3;
+                gamma_old = g;
+                alpha_old = alpha;
+            }
+            s_scal[0] = alpha;
+            s_scal[1] = beta;
+            s_dec = decision;
+        }
+        __syncthreads();
+        const double alpha = s_scal[0], beta = s_scal[1];
+        const int decision = s_dec;
+        __syncthreads();
+        if (decision == 3) {
+            if (gtid == 0) set_status(A.status, ST_NONFINITE);
+            break;
+        }
+        if (decision == 1) { converged = true; break; }
+        if (decision == 2) break;
+
+        const bool verify = decision == 4;
+        const bool refine = s_ref;
+        const float beta32 = (float)beta;
+        // ---- P phase.  The next reduction reads the slot of parity (it + 1);
+        // a verify step does not advance it, so its partials go to slot `par`
+        // (already read by every CTA two barriers ago).
+        double *npart = partials + (verify ? par : par ^ 1) * pstride;
+        gpart = 0.0;
+        rpart = 0.0;
+        for (int64_t i = row0 + threadIdx.x; i < row1; i += blockDim.x) {
+            double rr[3];
+            float pp[3], ss[3];
+            if (verify) {
+                // no Krylov step: only clear the rows that receive atomics
+                if (rowflag[i]) {
+                    w[3 * i] = 0.0f;
+                    w[3 * i + 1] = 0.0f;
+                    w[3 * i + 2] = 0.0f;
+                    ax[3 * i] = 0.0;
+                    ax[3 * i + 1] = 0.0;
+                    ax[3 * i + 2] = 0.0;
+                }
+                continue;
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float uu = __ldcg(u + 3 * i + c), ww = __ldcg(w + 3 * i + c);
+                pp[c] = fmaf(beta32, p[3 * i + c], uu);
+                ss[c] = fmaf(beta32, s[3 * i + c], ww);
+                p[3 * i + c] = pp[c];
+                s[3 * i + c] = ss[c];
+                x[3 * i + c] = fma(alpha, (double)pp[c], x[3 * i + c]);
+                rr[c] = fma(-alpha, (double)ss[c], r[3 * i + c]);
+                r[3 * i + c] = rr[c];
+            }
+            if (rowflag[i]) {
+                w[3 * i] = 0.0f;
+                w[3 * i + 1] = 0.0f;
+                w[3 * i + 2] = 0.0f;
+                if (refine) {
+                    ax[3 * i] = 0.0;
+                    ax[3 * i + 1] = 0.0;
+                    ax[3 * i + 2] = 0.0;
+                }
+            }
+            if (!refine) {
+                float uu[3];
+                precond32(A.dinv32 + 9 * i, rr, uu);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    u[3 * i + c] = uu[c];
+                    gpart = fma(rr[c], (double)uu[c], gpart);
+                    rpart = fma(rr[c], rr[c], rpart);
+                }
+            }
+        }
+        if (refine) {
+            // ---- residual replacement: r = b - A64 x with the FP64 master matrix
+            if (!grid_sync(count, nblocks, epoch, A.status)) { ok = false; break; }
+            double dummy = 0.0;
+            for (int64_t sl = gwarp; sl < nslices; sl += nwarps) {
+                unsigned char *fb = wbuf + (nb ^ 1) * kBufBytes;
+                issue_slice(fb, sl, nnz, A.val64, A.col, brow, lane);
+                cp_async_commit();
+                cp_async_wait<0>();
+                __syncwarp();
+                const int cnt = (int)min64(kSlice, nnz - sl * kSlice);
+                slice_spmv<double, false>(fb, cnt, x, ax, rowflag, join, lane, dummy);
+            }
+            if (!grid_sync(count, nblocks, epoch, A.status)) { ok = false; break; }
+            for (int64_t i = row0 + threadIdx.x; i < row1; i += blockDim.x) {
+                double rr[3];
+                float uu[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    rr[c] = fma(A.sign, A.b[3 * i + c], -__ldcg(ax + 3 * i + c));
+                    r[3 * i + c] = rr[c];
+                }
+                precond32(A.dinv32 + 9 * i, rr, uu);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    u[3 * i + c] = uu[c];
+                    gpart = fma(rr[c], (double)uu[c], gpart);
+                    rpart = fma(rr[c], rr[c], rpart);
+                }
+            }
+        }
+        {
+            double v[2] = {gpart, rpart};
+            cta_sum<2>(v, s_part, s_tot);
+            if (threadIdx.x == 0) {
+                npart[blockIdx.x * 4 + 0] = v[0];
+                npart[blockIdx.x * 4 + 1] = v[1];
+            }
+        }
+        if (!verify) ++it;
+        if (!grid_sync(count, nblocks, epoch, A.status)) { ok = false; break; }
+    }
+    cp_async_wait<0>();
+    if (gtid == 0 && (ok || it > 0)) {
+        *A.iters_dev = it;
+        *A.relres_dev = bnorm2 > 0.0 ? sqrt(rnorm2 / bnorm2) : 0.0;
+        if (ok && !converged) set_status(A.status, ST_NOT_CONVERGED);
+    }
+}
+
+}  // namespace
+
+const void *pcg_mixed_kernel_ptr() { return reinterpret_cast<const void *>(&pcg_mixed_kernel); }
+
+extern "C" int agipc_pcg_mixed(agipc_ctx *ctx, int32_t max_rows, const int32_t *n_rows_dev, const int32_t *row_ptr,
+                               const int32_t *col, const double *val, const float *val32, const float *dinv32,
+                               const double *b, double *x, const agipc_pcg_options *opt, int32_t refine_every,
+                               int32_t *iters_dev, double *relres_dev)
+{
+    if (!ctx || !opt || max_rows < 0 || max_rows > ctx->max_n || !n_rows_dev || !row_ptr || !val || !val32 ||
+        !dinv32 || !b || !x || !iters_dev || !relres_dev || refine_every < 0)
+        return AGIPC_ERR_INVALID_ARG;
+    if (!(opt->tol >= 0.0) || opt->max_iter < 0 || (opt->rhs_sign != 1 && opt->rhs_sign != -1))
+        return AGIPC_ERR_INVALID_ARG;
+    if (((uintptr_t)val & 15u) != 0 || ((uintptr_t)val32 & 15u) != 0 || ((uintptr_t)col & 15u) != 0 ||
+        ((uintptr_t)dinv32 & 3u) != 0 || ((uintptr_t)b & 7u) != 0 || ((uintptr_t)x & 7u) != 0)
+        return AGIPC_ERR_INVALID_ARG;
+    MixedArgs A;
+    A.n_dev = n_rows_dev;
+    A.rp = row_ptr;
+    A.col = col;
+    A.val64 = val;
+    A.val32 = val32;
+    A.dinv32 = dinv32;
+    A.b = b;
+    A.x = x;
+    A.sign = (double)opt->rhs_sign;
+    A.tol = opt->tol;
+    A.max_iter = opt->max_iter;
+    A.refine_every = refine_every;
+    A.max_rows = max_rows;
+    A.max_nnzb = ctx->max_nnzb;
+    A.iters_dev = iters_dev;
+    A.relres_dev = relres_dev;
+    A.S = ctx->pcg;
+    A.status = ctx->status;
+    if (cudaMemsetAsync(ctx->pcg.bar, 0, 64 * sizeof(unsigned), ctx->stream) != cudaSuccess) return AGIPC_ERR_CUDA;
+    void *args[] = {&A};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)pcg_mixed_kernel, dim3((unsigned)ctx->pcg_grid),
+                                                dim3(kPcgBlock), args, kPcgSmem, ctx->stream);
+    return e == cudaSuccess ? AGIPC_OK : AGIPC_ERR_CUDA;
+}
