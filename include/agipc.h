@@ -10,6 +10,10 @@
  *   agipc_pcg              H_c y = -g_c by block-Jacobi PCG      (Algorithm 1; Sec. 5, Preconditioners)
  *   agipc_prolongate       dx = U^T y                            (Sec. 4.3)
  *
+ * plus the precision form (agipc_*_mixed), the differentiation form
+ * (agipc_fine_assemble_stvk, agipc_restrict, agipc_stvk_vjp) and
+ * agipc_prolongate_add, agipc_aggregate_static.
+ *
  * Conventions for every call:
  *   - All array arguments are DEVICE pointers owned by the caller; the
  *     library never frees them.  Scratch memory belongs to the context and is
@@ -189,6 +193,87 @@ int agipc_pcg_mixed(agipc_ctx *ctx, int32_t max_rows, const int32_t *n_rows_dev,
  *   n_fine, labels [n_fine], y [n_c][3]  ->  dx [n_fine][3]
  */
 int agipc_prolongate(agipc_ctx *ctx, int32_t n_fine, const int32_t *labels, const double *y, double *dx);
+
+/*
+ * Prolongation followed by the Newton update (Sec. 4.3 and Algorithm 1,
+ * x <- x + d_f at unit step length): out[f] = base[f] + y[labels[f]].
+ * base and out may alias.  Arguments and statuses as agipc_prolongate.
+ */
+int agipc_prolongate_add(agipc_ctx *ctx, int32_t n_fine, const int32_t *labels, const double *y,
+                         const double *base, double *out);
+
+/*
+ * Differentiation form.  The coarsened step x_next = x + U^T y with
+ * y = -(U H U^T)^-1 U g is a function of per-tet Young's moduli E and of the
+ * rest positions X_rest through the elastic terms of the incremental
+ * potential (Eq. 1 divided by dt^2); the labels are piecewise constant in
+ * both, so they carry no derivative (Galerkin coarse operator, Sec. 4.1).
+ * For a loss with v = dL/dx_next the adjoint is
+ *     H_c lambda_c = U v   (agipc_restrict, then agipc_pcg with rhs_sign +1),
+ *     lambda = U^T lambda_c (agipc_prolongate),
+ *     dL/dtheta = -lambda^T (dg/dtheta + dH/dtheta dx)   (agipc_stvk_vjp).
+ *
+ * Elasticity is St. Venant-Kirchhoff: Psi_e = V_e (mu |G|_F^2 + lam/2 tr(G)^2),
+ * G = (F^T F - I)/2, F = Ds Dm^-1, mu = E/(2(1+nu)), lam = E nu/((1+nu)(1-2nu)),
+ * V_e = |det Dm|/6; each tet's 12x12 Hessian is made PSD by clamping its
+ * eigenvalues at zero before it is summed.
+ */
+
+/*
+ * Fine Newton system of StVK tets (Eq. 1 divided by dt^2):
+ *   H = M/h^2 + sum_e H_e+,   g = M/h^2 (x - x_hat) + sum_e dPsi_e/dx + g_extra
+ * with the inertial target x_hat = X_rest + xhat_shift (h^2 gravity for a
+ * body starting at rest; a velocity term h v is constant in the parameters
+ * and belongs in g_extra as -M/h v), written into the VALUES of a given
+ * upper BSR structure.
+ *   n_fine, n_tets, tets [n_tets][4]   vertices of each tet
+ *   X_rest, x [n_fine][3]              rest positions, current positions
+ *   xhat_shift                         HOST array of 3 doubles
+ *   E [n_tets], nu                     Young's modulus per tet, Poisson ratio in (-1, 0.5)
+ *   mass_h2 [n_fine]                   lumped mass / h^2
+ *   g_extra [n_fine][3] or NULL        further gradient terms (e.g. contact), added as is
+ *   fine_row_ptr [n_fine+1], fine_col  upper BSR structure (column >= row, sorted,
+ *                                      diagonal first in each row) that holds every
+ *                                      vertex pair of every tet
+ *   fine_val [fine_nnzb][9]            out: H (upper blocks); g [n_fine][3] out
+ * Blocks absent from the structure, or tet vertices out of range or repeated,
+ * set AGIPC_ERR_BAD_INDEX; a non-finite element gradient sets
+ * AGIPC_ERR_NONFINITE.  Summation uses atomics, so the last bits of the sums
+ * depend on scheduling.  fine_nnzb is capped by the context's max_fine_nnzb.
+ */
+int agipc_fine_assemble_stvk(agipc_ctx *ctx, int32_t n_fine, int64_t n_tets, const int32_t *tets,
+                             const double *X_rest, const double *x, const double *xhat_shift, const double *E, double nu,
+                             const double *mass_h2, const double *g_extra, const int32_t *fine_row_ptr,
+                             const int32_t *fine_col, int64_t fine_nnzb, double *fine_val, double *g);
+
+/*
+ * Restriction v_c = U v (the map of Sec. 4.1 applied to a fine vector):
+ * v_c[c] = sum over labels[f] == c of v[f].
+ *   v [n_fine][3]; v_c [n_fine][3] out (rows past n_c are zeroed)
+ * Labels outside [0, n_c) set AGIPC_ERR_BAD_INDEX.
+ */
+int agipc_restrict(agipc_ctx *ctx, int32_t n_fine, const int32_t *labels, const int32_t *n_coarse_dev,
+                   const double *v, double *v_c);
+
+/*
+ * Per-element vector-Jacobian product of the step, given the prolongated
+ * adjoint lambda and the step dx:
+ *   dL_dE[e]      = -lambda_e^T (g_e + H_e+ dx_e) / E_e   (Psi_e is linear in
+ *                   E_e and the clamp commutes with positive scaling)
+ *   dL_dX_rest    = -d/dX_rest [lambda^T g + lambda^T H+ dx] + lambda M/h^2
+ * The derivative of the clamp goes through the element's eigen-
+ * decomposition H_e = V diag(l) V^T: lambda^T dH+ dx = <dH, V (F o a b^T) V^T>,
+ * a = V^T lambda_e, b = V^T dx_e, F the divided differences of max(., 0)
+ * over the eigenvalues.  The last term comes from the inertial target
+ * x_hat = X_rest + xhat_shift of agipc_fine_assemble_stvk; pass
+ * mass_h2 = NULL to leave it out.  Masses are constants; x is data, not a
+ * parameter.
+ *   lam, dx [n_fine][3]; dL_dE [n_tets] out; dL_dX_rest [n_fine][3] out
+ * Other arguments as agipc_fine_assemble_stvk.
+ */
+int agipc_stvk_vjp(agipc_ctx *ctx, int32_t n_fine, int64_t n_tets, const int32_t *tets, const double *X_rest,
+                   const double *x, const double *E, double nu, const double *mass_h2, const double *lam,
+                   const double *dx, double *dL_dE, double *dL_dX_rest);
 
 /*
  * Labeller without allocation.  The paper has no counterpart: this is a

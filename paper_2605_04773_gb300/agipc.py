@@ -70,11 +70,18 @@ def load():
     lib.agipc_assemble_coarse_mixed.argtypes = [P, i32, P, P, P, P, P, i64, i64, P, P, i64, P, P, P, P, P, P, P, i64,
                                                 P, P, P]
     lib.agipc_pcg_mixed.argtypes = [P, i32, P, P, P, P, P, P, P, P, ctypes.POINTER(_PcgOptions), i32, P, P]
+    f64 = ctypes.c_double
+    D3 = ctypes.POINTER(ctypes.c_double)
+    lib.agipc_prolongate_add.argtypes = [P, i32, P, P, P, P]
+    lib.agipc_fine_assemble_stvk.argtypes = [P, i32, i64, P, P, P, D3, P, f64, P, P, P, P, i64, P, P]
+    lib.agipc_restrict.argtypes = [P, i32, P, P, P, P]
+    lib.agipc_stvk_vjp.argtypes = [P, i32, i64, P, P, P, P, f64, P, P, P, P, P]
     lib.agipc_status_string.argtypes = [ctypes.c_int]
     lib.agipc_status_string.restype = ctypes.c_char_p
     for name in ("agipc_create", "agipc_destroy", "agipc_set_stream", "agipc_aggregate", "agipc_assemble_coarse",
                  "agipc_pcg", "agipc_prolongate", "agipc_status", "agipc_aggregate_static",
-                 "agipc_assemble_coarse_mixed", "agipc_pcg_mixed"):
+                 "agipc_assemble_coarse_mixed", "agipc_pcg_mixed", "agipc_prolongate_add", "agipc_fine_assemble_stvk",
+                 "agipc_restrict", "agipc_stvk_vjp"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -185,6 +192,31 @@ def agipc_pcg_mixed(ctx: Context, max_rows: int, n_rows_dev, row_ptr, col, val, 
     _check(load().agipc_pcg_mixed(ctx.handle, int(max_rows), _ptr(n_rows_dev), _ptr(row_ptr), _ptr(col), _ptr(val),
                                   _ptr(val32), _ptr(dinv32), _ptr(b), _ptr(x), ctypes.byref(opt), int(refine_every),
                                   _ptr(iters_dev), _ptr(relres_dev)), "agipc_pcg_mixed")
+
+
+def agipc_prolongate_add(ctx: Context, n_fine: int, labels, y, base, out):
+    _check(load().agipc_prolongate_add(ctx.handle, int(n_fine), _ptr(labels), _ptr(y), _ptr(base), _ptr(out)),
+           "agipc_prolongate_add")
+
+
+def agipc_fine_assemble_stvk(ctx: Context, n_fine: int, tets, X_rest, x, xhat_shift, E, nu: float, mass_h2,
+                             g_extra, fine_row_ptr, fine_col, fine_val, g):
+    shift = (ctypes.c_double * 3)(*[float(v) for v in xhat_shift])
+    _check(load().agipc_fine_assemble_stvk(
+        ctx.handle, int(n_fine), int(tets.shape[0]), _ptr(tets), _ptr(X_rest), _ptr(x), shift, _ptr(E), float(nu),
+        _ptr(mass_h2), _ptr(g_extra), _ptr(fine_row_ptr), _ptr(fine_col), int(fine_col.shape[0]), _ptr(fine_val),
+        _ptr(g)), "agipc_fine_assemble_stvk")
+
+
+def agipc_restrict(ctx: Context, n_fine: int, labels, n_coarse_dev, v, v_c):
+    _check(load().agipc_restrict(ctx.handle, int(n_fine), _ptr(labels), _ptr(n_coarse_dev), _ptr(v), _ptr(v_c)),
+           "agipc_restrict")
+
+
+def agipc_stvk_vjp(ctx: Context, n_fine: int, tets, X_rest, x, E, nu: float, mass_h2, lam, dx, dL_dE, dL_dX_rest):
+    _check(load().agipc_stvk_vjp(ctx.handle, int(n_fine), int(tets.shape[0]), _ptr(tets), _ptr(X_rest), _ptr(x),
+                                 _ptr(E), float(nu), _ptr(mass_h2), _ptr(lam), _ptr(dx), _ptr(dL_dE),
+                                 _ptr(dL_dX_rest)), "agipc_stvk_vjp")
 
 
 AGGREGATE_STATIC_MAX_NODES = 1 << 20
@@ -345,3 +377,126 @@ class FineStep:
 
     def host(self):
         return self.inner.host()
+
+
+# ---------------------------------------------------------------------------
+# Differentiation form
+# ---------------------------------------------------------------------------
+
+GRAVITY = (0.0, 0.0, -9.81)
+
+
+class DiffDeviceProblem:
+    """The differentiation form's constant inputs on the device: topology,
+    fine upper BSR structure, current positions, M/h^2, contact terms."""
+
+    def __init__(self, problem: dict, device="cuda"):
+        t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(device=device, dtype=dt)  # noqa: E731
+        self.n = int(problem["n"])
+        self.nu = float(problem["nu"])
+        self.h = float(problem["h"])
+        self.tets = t(problem["tets"], torch.int32)
+        self.edges = t(problem["edges"], torch.int32)
+        self.tags = t(problem["tags"], torch.uint8)
+        self.row_ptr = t(problem["row_ptr"], torch.int32)
+        self.col = t(problem["col"], torch.int32)
+        self.x = t(problem["x"], torch.float64)
+        self.mass_h2 = t(problem["mass_h2"], torch.float64)
+        self.pair_idx = t(np.asarray(problem["pair_idx"]).reshape(-1, 4), torch.int32)
+        self.pair_blk = t(np.asarray(problem["pair_blk"]).reshape(-1, 90), torch.float64)
+        gp = problem.get("g_pairs")
+        self.g_extra = None if gp is None or not np.any(gp) else t(gp, torch.float64)
+        self.xhat_shift = tuple(self.h * self.h * gv for gv in GRAVITY)
+
+    @property
+    def capacity(self) -> int:
+        return 2 * int(self.col.shape[0]) + 16 * int(self.pair_idx.shape[0])
+
+    def context(self) -> Context:
+        return Context(self.n, self.edges.shape[0], self.col.shape[0], max(1, self.pair_idx.shape[0]))
+
+
+class DiffStep:
+    """Buffers and calls of the differentiation form.
+
+    forward(E, X_rest): fine StVK assembly -> labels -> coarse assembly ->
+    PCG -> x_next = x + U^T y.  backward(v): v_c = U v -> PCG on the same
+    coarse system -> lambda = U^T lambda_c -> per-element VJP."""
+
+    def __init__(self, ctx: Context, dp: DiffDeviceProblem, tol: float, max_iter: int = 100000,
+                 adjoint_tol: float = None):
+        dev = dp.x.device
+        n, cap = dp.n, dp.capacity
+        i32 = dict(device=dev, dtype=torch.int32)
+        f64 = dict(device=dev, dtype=torch.float64)
+        self.ctx, self.dp, self.tol, self.max_iter = ctx, dp, tol, max_iter
+        self.adjoint_tol = tol if adjoint_tol is None else adjoint_tol
+        self.fine_val = torch.empty(dp.col.shape[0], 9, **f64)
+        self.g = torch.empty(n, 3, **f64)
+        self.labels = torch.empty(n, **i32)
+        self.n_c = torch.zeros(1, **i32)
+        self.row_ptr = torch.empty(n + 1, **i32)
+        self.col = torch.empty(cap, **i32)
+        self.val = torch.empty(cap, 9, **f64)
+        self.nnz = torch.zeros(1, **i32)
+        self.g_c = torch.empty(n, 3, **f64)
+        self.dinv = torch.empty(n, 9, **f64)
+        self.y = torch.empty(n, 3, **f64)
+        self.x_next = torch.empty(n, 3, **f64)
+        self.dx = torch.empty(n, 3, **f64)
+        self.iters = torch.zeros(1, **i32)
+        self.relres = torch.zeros(1, **f64)
+        self.v_c = torch.empty(n, 3, **f64)
+        self.lam_c = torch.empty(n, 3, **f64)
+        self.lam = torch.empty(n, 3, **f64)
+        self.adj_iters = torch.zeros(1, **i32)
+        self.adj_relres = torch.zeros(1, **f64)
+        self.dL_dE = torch.empty(dp.tets.shape[0], **f64)
+        self.dL_dX = torch.empty(n, 3, **f64)
+        self.E = None
+        self.X_rest = None
+
+    def forward(self, E, X_rest):
+        dp, ctx = self.dp, self.ctx
+        self.E, self.X_rest = E, X_rest
+        agipc_fine_assemble_stvk(ctx, dp.n, dp.tets, X_rest, dp.x, dp.xhat_shift, E, dp.nu, dp.mass_h2, dp.g_extra,
+                                 dp.row_ptr, dp.col, self.fine_val, self.g)
+        agipc_aggregate(ctx, dp.n, dp.edges, dp.tags, self.labels, self.n_c)
+        agipc_assemble_coarse(ctx, dp.n, self.labels, self.n_c, dp.row_ptr, dp.col, self.fine_val, dp.pair_idx,
+                              dp.pair_blk, self.g, self.row_ptr, self.col, self.val, self.nnz, self.g_c, self.dinv)
+        agipc_pcg(ctx, dp.n, self.n_c, self.row_ptr, self.col, self.val, self.dinv, self.g_c, self.y, self.tol,
+                  self.max_iter, -1, self.iters, self.relres)
+        agipc_prolongate(ctx, dp.n, self.labels, self.y, self.dx)
+        agipc_prolongate_add(ctx, dp.n, self.labels, self.y, dp.x, self.x_next)
+        return self.x_next
+
+    def backward(self, v):
+        dp, ctx = self.dp, self.ctx
+        v = v.contiguous()
+        agipc_restrict(ctx, dp.n, self.labels, self.n_c, v, self.v_c)
+        agipc_pcg(ctx, dp.n, self.n_c, self.row_ptr, self.col, self.val, self.dinv, self.v_c, self.lam_c,
+                  self.adjoint_tol, self.max_iter, 1, self.adj_iters, self.adj_relres)
+        agipc_prolongate(ctx, dp.n, self.labels, self.lam_c, self.lam)
+        agipc_stvk_vjp(ctx, dp.n, dp.tets, self.X_rest, dp.x, self.E, dp.nu, dp.mass_h2, self.lam, self.dx,
+                       self.dL_dE, self.dL_dX)
+        return self.dL_dE, self.dL_dX
+
+
+class CoarsenedStepFunction(torch.autograd.Function):
+    """x_next = step(E, X_rest) with the hand-written adjoint as backward.
+    Aggregation is piecewise constant in the parameters; x is data."""
+
+    @staticmethod
+    def forward(fctx, E, X_rest, step: DiffStep):
+        fctx.step = step
+        return step.forward(E.detach().contiguous(), X_rest.detach().contiguous()).clone()
+
+    @staticmethod
+    def backward(fctx, grad_x_next):
+        dE, dX = fctx.step.backward(grad_x_next)
+        return dE.clone(), dX.clone(), None
+
+
+def coarsened_step(E, X_rest, step: DiffStep):
+    """Differentiable coarsened Newton step (see CoarsenedStepFunction)."""
+    return CoarsenedStepFunction.apply(E, X_rest, step)

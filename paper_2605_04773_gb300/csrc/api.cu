@@ -56,7 +56,7 @@ void carve_all(agipc_ctx *c, char *base, size_t *total)
 }
 
 __global__ void prolongate_kernel(int32_t n, const int32_t *__restrict__ labels, const double *__restrict__ y,
-                                  double *__restrict__ dx, uint32_t *status)
+                                  const double *__restrict__ base, double *__restrict__ dx, uint32_t *status)
 {
     const int64_t m = 3 * (int64_t)n;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
@@ -68,7 +68,8 @@ __global__ void prolongate_kernel(int32_t n, const int32_t *__restrict__ labels,
             dx[e] = 0.0;
             continue;
         }
-        dx[e] = y[3 * (int64_t)lab + c];
+        const double v = y[3 * (int64_t)lab + c];
+        dx[e] = base ? base[e] + v : v;
     }
 }
 
@@ -199,6 +200,19 @@ extern "C" int agipc_prolongate(agipc_ctx *ctx, int32_t n_fine, const int32_t *l
     const int tb = 256;
     const int64_t m = 3 * (int64_t)n_fine;
     const unsigned grid = (unsigned)std::min<int64_t>(div_up(m, tb), (int64_t)ctx->num_sms * 32);
-    prolongate_kernel<<<grid, tb, 0, ctx->stream>>>(n_fine, labels, y, dx, ctx->status);
+    prolongate_kernel<<<grid, tb, 0, ctx->stream>>>(n_fine, labels, y, nullptr, dx, ctx->status);
+    return cudaPeekAtLastError() == cudaSuccess ? AGIPC_OK : AGIPC_ERR_CUDA;
+}
+
+extern "C" int agipc_prolongate_add(agipc_ctx *ctx, int32_t n_fine, const int32_t *labels, const double *y,
+                                    const double *base, double *out)
+{
+    if (!ctx || n_fine < 0 || n_fine > ctx->max_n || (n_fine > 0 && (!labels || !y || !base || !out)))
+        return AGIPC_ERR_INVALID_ARG;
+    if (n_fine == 0) return AGIPC_OK;
+    const int tb = 256;
+    const int64_t m = 3 * (int64_t)n_fine;
+    const unsigned grid = (unsigned)std::min<int64_t>(div_up(m, tb), (int64_t)ctx->num_sms * 32);
+    prolongate_kernel<<<grid, tb, 0, ctx->stream>>>(n_fine, labels, y, base, out, ctx->status);
     return cudaPeekAtLastError() == cudaSuccess ? AGIPC_OK : AGIPC_ERR_CUDA;
 }

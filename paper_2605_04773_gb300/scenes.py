@@ -358,14 +358,16 @@ def build_scene(name: str, seed: int, bodies: list, nu: float, rho: float, h: fl
         sel = rng.choice(d.size, size=k, replace=False)
         d = d.copy()
         d[sel] = rng.uniform(0.01, 0.05, size=k) * dhat
+    g_pairs = np.zeros((n, 3))
     if pidx.shape[0]:
         pgrad, pblk = barrier_stencils(grad_d, d, dhat, kappa) if np.isscalar(kappa) else \
             _barrier_stencils_vec(grad_d, d, dhat, kappa)
-        g += _scatter_grad(n, pidx, pgrad.reshape(-1, 4, 3))
+        g_pairs = _scatter_grad(n, pidx, pgrad.reshape(-1, 4, 3))
+        g += g_pairs
     else:
         pblk = np.zeros((0, 10, 3, 3))
     meta = dict(X_rest=X, x=x, x_hat=x_hat, tets=tets, E_elem=E_t, nu=nu, rho=rho, h=h, dhat=dhat,
-                mass=mass, pair_d=d, bodies=body_info, vol=vol)
+                mass=mass, pair_d=d, bodies=body_info, vol=vol, g_pairs=g_pairs)
     if keep_elements:
         meta.update(elem_grad=e_grad, elem_hess=e_hess, pair_grad_d=grad_d, pair_kappa=kappa)
     return Scene(name=name, seed=seed, n=n, edges=edges, tags=tags, row_ptr=row_ptr, col=col,
@@ -535,3 +537,50 @@ def precision_inputs(sc: Scene, fp64_gap: float = 0.05) -> dict:
                 pair_blk32=np.ascontiguousarray(sc.pair_blk[~small].astype(np.float32)),
                 pair_idx64=np.ascontiguousarray(sc.pair_idx[small]),
                 pair_blk64=np.ascontiguousarray(sc.pair_blk[small]))
+
+
+def _no_pairs(rng, body_info):
+    return np.zeros((0, 4), np.int32), np.zeros((0, 12)), np.zeros(0), 1.0
+
+
+def diff_grid(seed: int = 1005, n_cells: int = 46, E_mean: float = 1e5, E_log_sigma: float = 0.5,
+              frac: float = 0.7, target_sigma: float = 0.05, pairs: int = 0) -> Scene:
+    """The differentiation workload: one n^3 hex grid of side 1 m (46^3:
+    103,823 vertices, 584,016 tets), a per-tet Young's modulus drawn
+    log-normal around E_mean (log-sd E_log_sigma), nu = 0.4, h = 1/60 s, 70 %
+    of edges collapsible, no barrier pairs unless ``pairs`` > 0 (point-
+    triangle stencils, constant in the parameters), and a target position
+    field x_target = x + target_sigma * cell * N(0, 1) for the loss
+    L = |x_next - x_target|^2."""
+    rng = np.random.default_rng(seed + 104729)
+    nt = 6 * n_cells ** 3
+    E_t = E_mean * np.exp(E_log_sigma * rng.standard_normal(nt))
+    dhat = 1e-3
+    if pairs:
+        fn = _random_pairs_in_body(pairs)
+        fn.dhat = dhat
+    else:
+        fn = _no_pairs
+    body = Body(n_cells, n_cells, n_cells, 1.0 / n_cells, (0.0, 0.0, 0.0), E_mean, frac)
+    sc = build_scene("diff_grid_%d" % n_cells, seed, [body], nu=0.4, rho=1000.0, h=1.0 / 60.0, dhat=dhat,
+                     pair_fn=fn, E_elem=E_t)
+    cell = 1.0 / n_cells
+    sc.meta["x_target"] = sc.meta["x"] + target_sigma * cell * rng.standard_normal(sc.meta["x"].shape)
+    return sc
+
+
+def diff_problem(sc: Scene) -> dict:
+    """The inputs of the differentiation form from a scene: topology, the
+    fine upper BSR structure, current positions, parameters (E per tet,
+    X_rest), M/h^2, the constant contact terms and the loss target."""
+    m = sc.meta
+    h = m["h"]
+    x_target = m.get("x_target")
+    if x_target is None:
+        rng = np.random.default_rng(sc.seed + 15485863)
+        cell = min(b["cell"] for b in m["bodies"])
+        x_target = m["x"] + 0.05 * cell * rng.standard_normal(m["x"].shape)
+    return dict(n=sc.n, tets=np.ascontiguousarray(m["tets"], dtype=np.int32), edges=sc.edges, tags=sc.tags,
+                row_ptr=sc.row_ptr, col=sc.col, x=m["x"], X_rest=m["X_rest"], E=np.asarray(m["E_elem"]),
+                nu=m["nu"], h=h, mass_h2=m["mass"] / (h * h), pair_idx=sc.pair_idx, pair_blk=sc.pair_blk,
+                g_pairs=m["g_pairs"], x_target=x_target)
