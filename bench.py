@@ -236,9 +236,11 @@ def run_ours(args):
     # ---- precision form (FP32 blocks/SpMV/preconditioner, FP64 dots and
     # residual replacement every 20 iterations, small-gap stencils in FP64) on
     # the same workload with 1% of the barrier gaps redrawn below 0.05 dhat
-    prec = None
+    prec = diff = None
     if not args.skip_forms:
         prec = precision_form(ctx_factory=lambda d: d.context(), dev=dev, steps=min(args.steps, 20))
+        # ---- differentiation form (forward step + adjoint + per-tet VJP)
+        diff = differentiation_form(dev, steps=min(args.steps, 10))
 
     # ---- max over ranks
     if ws > 1:
@@ -286,6 +288,7 @@ def run_ours(args):
             "gpu_launches": sum(KERNELS_PER_STEP.values()) * args.steps,
             "clocks": clocks,
             "precision_form": prec,
+            "differentiation_form": diff,
             "wall_s_timed_region": t_wall,
         }
         if ws == 1 and not args.no_cpu_baseline:
@@ -321,8 +324,17 @@ def precision_form(ctx_factory, dev, steps: int):
     ctx.check()
     ms = float(np.median([a.elapsed_time(b) for a, b in ev]))
     m = mixed.host()
+    # the FP64 path on the same scene, same timing
     full.run()
     ctx.check()
+    for a, b in ev:
+        l2.fill_(1.0)
+        a.record(stream)
+        full.run()
+        b.record(stream)
+    torch.cuda.synchronize(dev)
+    ctx.check()
+    ms64 = float(np.median([a.elapsed_time(b) for a, b in ev]))
     f = full.host()
     # errors against the FP64 path on the unrounded inputs
     gc, y32, crp, cci, cval = f["g_c"], m["y"], f["row_ptr"], f["col"], f["val"]
@@ -344,13 +356,86 @@ def precision_form(ctx_factory, dev, steps: int):
     e64, e32 = dE(f["dx"]), dE(m["dx"])
     pi = scenes.precision_inputs(sc)
     ctx.close()
-    return {"value": 1e3 / ms, "unit": UNIT, "ms_per_step": ms, "pcg_iters": m["iters"], "workload":
+    return {"value": 1e3 / ms, "unit": UNIT, "ms_per_step": ms, "pcg_iters": m["iters"],
+            "fp64_same_scene": {"value": 1e3 / ms64, "ms_per_step": ms64, "pcg_iters": f["iters"]}, "workload":
             "domino_8x8 with 1% of barrier gaps in (0.01, 0.05) dhat (seed 1003), tol 1e-6, refinement every 20",
             "fp64_stencils": int(pi["pair_idx64"].shape[0]),
             "dx_rel_err_vs_fp64": float(np.linalg.norm(m["dx"] - f["dx"]) / np.linalg.norm(f["dx"])),
             "coarse_fp64_residual": float(res32), "fp64_path_residual": f["relres"],
             "energy_decrease_fp64": e64, "energy_decrease_mixed": e32,
             "energy_decrease_rel_err": abs(e32 - e64) / abs(e64)}
+
+
+def differentiation_form(dev, steps: int):
+    """Time one differentiable coarsened step on the 46^3 StVK grid with a
+    log-normal Young's modulus field: forward (fine StVK assembly with PSD
+    projection, labels, coarse assembly, PCG, x + U^T y) and backward
+    (restriction, adjoint PCG on the same coarse system, prolongation,
+    per-tet VJP), both to the headline tolerance."""
+    import torch
+    from paper_2605_04773_gb300 import agipc, scenes
+    sc = scenes.diff_grid()
+    pr = scenes.diff_problem(sc)
+    dp = agipc.DiffDeviceProblem(pr, dev)
+    ctx = dp.context()
+    step = agipc.DiffStep(ctx, dp, tol=TOL)
+    E = torch.tensor(pr["E"], dtype=torch.float64, device=dev)
+    X = torch.tensor(pr["X_rest"], dtype=torch.float64, device=dev)
+    xt = torch.tensor(pr["x_target"], dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    v = torch.empty_like(xt)
+    for _ in range(3):
+        x_next = step.forward(E, X)
+        torch.mul(torch.sub(x_next, xt), 2.0, out=v)
+        step.backward(v)
+    ctx.check()
+    l2 = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    names = ("fine_assemble_stvk", "coarse_step", "adjoint", "stvk_vjp")
+    rec = {k: [] for k in names + ("forward", "backward")}
+    for _ in range(steps):
+        l2.fill_(1.0)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        ev[0].record(stream)
+        agipc.agipc_fine_assemble_stvk(ctx, dp.n, dp.tets, X, dp.x, dp.xhat_shift, E, dp.nu, dp.mass_h2,
+                                       dp.g_extra, dp.row_ptr, dp.col, step.fine_val, step.g, step.workspace)
+        ev[1].record(stream)
+        agipc.agipc_aggregate(ctx, dp.n, dp.edges, dp.tags, step.labels, step.n_c)
+        agipc.agipc_assemble_coarse(ctx, dp.n, step.labels, step.n_c, dp.row_ptr, dp.col, step.fine_val,
+                                    dp.pair_idx, dp.pair_blk, step.g, step.row_ptr, step.col, step.val, step.nnz,
+                                    step.g_c, step.dinv)
+        agipc.agipc_pcg(ctx, dp.n, step.n_c, step.row_ptr, step.col, step.val, step.dinv, step.g_c, step.y,
+                        step.tol, step.max_iter, -1, step.iters, step.relres)
+        agipc.agipc_prolongate(ctx, dp.n, step.labels, step.y, step.dx)
+        agipc.agipc_prolongate_add(ctx, dp.n, step.labels, step.y, dp.x, step.x_next)
+        ev[2].record(stream)
+        torch.mul(torch.sub(step.x_next, xt), 2.0, out=v)
+        ev[3].record(stream)
+        agipc.agipc_restrict(ctx, dp.n, step.labels, step.n_c, v, step.v_c)
+        agipc.agipc_pcg(ctx, dp.n, step.n_c, step.row_ptr, step.col, step.val, step.dinv, step.v_c, step.lam_c,
+                        step.adjoint_tol, step.max_iter, 1, step.adj_iters, step.adj_relres)
+        agipc.agipc_prolongate(ctx, dp.n, step.labels, step.lam_c, step.lam)
+        ev[4].record(stream)
+        agipc.agipc_stvk_vjp(ctx, dp.n, dp.tets, X, dp.x, E, dp.nu, dp.mass_h2, step.lam, step.dx, step.dL_dE,
+                             step.dL_dX, step.workspace)
+        ev[5].record(stream)
+        torch.cuda.synchronize(dev)
+        for k, (i, j) in zip(names, ((0, 1), (1, 2), (3, 4), (4, 5))):
+            rec[k].append(ev[i].elapsed_time(ev[j]))
+        rec["forward"].append(ev[0].elapsed_time(ev[2]))
+        rec["backward"].append(ev[3].elapsed_time(ev[5]))
+    ctx.check()
+    med = {k: float(np.median(v_)) for k, v_ in rec.items()}
+    ws = step.workspace
+    n_flag = int(ws[0].item() & 0xFFFFFFFF)
+    out = {"value": 1e3 / (med["forward"] + med["backward"]), "unit": "gradient evaluations/s",
+           "ms_forward": med["forward"], "ms_backward": med["backward"],
+           "ms": {k: med[k] for k in names}, "pcg_iters": int(step.iters.item()),
+           "adjoint_iters": int(step.adj_iters.item()), "n_c": int(step.n_c.item()),
+           "flagged_tets_last_vjp": n_flag, "n_tets": int(dp.tets.shape[0]),
+           "workload": "46^3 Kuhn grid (103,823 vertices, 584,016 tets), log-normal E around 1e5 Pa, "
+                       "70% collapsible, FP64, PCG and adjoint PCG to 1e-6"}
+    ctx.close()
+    return out
 
 
 def cpu_baseline(sc, reps: int = 1):

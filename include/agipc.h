@@ -236,6 +236,10 @@ int agipc_prolongate_add(agipc_ctx *ctx, int32_t n_fine, const int32_t *labels, 
  *                                      diagonal first in each row) that holds every
  *                                      vertex pair of every tet
  *   fine_val [fine_nnzb][9]            out: H (upper blocks); g [n_fine][3] out
+ *   workspace, workspace_bytes         caller-owned device scratch, 128-byte aligned,
+ *                                      at least agipc_stvk_workspace_bytes(n_tets) bytes
+ *                                      (the list of tets whose Hessian is not clearly
+ *                                      positive definite); n_tets <= INT32_MAX
  * Blocks absent from the structure, or tet vertices out of range or repeated,
  * set AGIPC_ERR_BAD_INDEX; a non-finite element gradient sets
  * AGIPC_ERR_NONFINITE.  Summation uses atomics, so the last bits of the sums
@@ -244,7 +248,8 @@ int agipc_prolongate_add(agipc_ctx *ctx, int32_t n_fine, const int32_t *labels, 
 int agipc_fine_assemble_stvk(agipc_ctx *ctx, int32_t n_fine, int64_t n_tets, const int32_t *tets,
                              const double *X_rest, const double *x, const double *xhat_shift, const double *E, double nu,
                              const double *mass_h2, const double *g_extra, const int32_t *fine_row_ptr,
-                             const int32_t *fine_col, int64_t fine_nnzb, double *fine_val, double *g);
+                             const int32_t *fine_col, int64_t fine_nnzb, double *fine_val, double *g, void *workspace,
+                             int64_t workspace_bytes);
 
 /*
  * Restriction v_c = U v (the map of Sec. 4.1 applied to a fine vector):
@@ -269,11 +274,16 @@ int agipc_restrict(agipc_ctx *ctx, int32_t n_fine, const int32_t *labels, const 
  * mass_h2 = NULL to leave it out.  Masses are constants; x is data, not a
  * parameter.
  *   lam, dx [n_fine][3]; dL_dE [n_tets] out; dL_dX_rest [n_fine][3] out
- * Other arguments as agipc_fine_assemble_stvk.
+ * Other arguments (workspace included) as agipc_fine_assemble_stvk.  The
+ * per-tet terms are summed with atomics.
  */
 int agipc_stvk_vjp(agipc_ctx *ctx, int32_t n_fine, int64_t n_tets, const int32_t *tets, const double *X_rest,
                    const double *x, const double *E, double nu, const double *mass_h2, const double *lam,
-                   const double *dx, double *dL_dE, double *dL_dX_rest);
+                   const double *dx, double *dL_dE, double *dL_dX_rest, void *workspace, int64_t workspace_bytes);
+
+/* Bytes of device workspace agipc_fine_assemble_stvk and agipc_stvk_vjp
+ * need for n_tets tets (-1 for a negative count). */
+int64_t agipc_stvk_workspace_bytes(int64_t n_tets);
 
 /*
  * Labeller without allocation.  The paper has no counterpart: this is a

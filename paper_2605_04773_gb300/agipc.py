@@ -73,9 +73,11 @@ def load():
     f64 = ctypes.c_double
     D3 = ctypes.POINTER(ctypes.c_double)
     lib.agipc_prolongate_add.argtypes = [P, i32, P, P, P, P]
-    lib.agipc_fine_assemble_stvk.argtypes = [P, i32, i64, P, P, P, D3, P, f64, P, P, P, P, i64, P, P]
+    lib.agipc_fine_assemble_stvk.argtypes = [P, i32, i64, P, P, P, D3, P, f64, P, P, P, P, i64, P, P, P, i64]
     lib.agipc_restrict.argtypes = [P, i32, P, P, P, P]
-    lib.agipc_stvk_vjp.argtypes = [P, i32, i64, P, P, P, P, f64, P, P, P, P, P]
+    lib.agipc_stvk_vjp.argtypes = [P, i32, i64, P, P, P, P, f64, P, P, P, P, P, P, i64]
+    lib.agipc_stvk_workspace_bytes.argtypes = [i64]
+    lib.agipc_stvk_workspace_bytes.restype = i64
     lib.agipc_status_string.argtypes = [ctypes.c_int]
     lib.agipc_status_string.restype = ctypes.c_char_p
     for name in ("agipc_create", "agipc_destroy", "agipc_set_stream", "agipc_aggregate", "agipc_assemble_coarse",
@@ -199,13 +201,19 @@ def agipc_prolongate_add(ctx: Context, n_fine: int, labels, y, base, out):
            "agipc_prolongate_add")
 
 
+def stvk_workspace(n_tets: int, device="cuda"):
+    """A device workspace for agipc_fine_assemble_stvk / agipc_stvk_vjp."""
+    nbytes = int(load().agipc_stvk_workspace_bytes(int(n_tets)))
+    return torch.empty((nbytes + 7) // 8, dtype=torch.int64, device=device)
+
+
 def agipc_fine_assemble_stvk(ctx: Context, n_fine: int, tets, X_rest, x, xhat_shift, E, nu: float, mass_h2,
-                             g_extra, fine_row_ptr, fine_col, fine_val, g):
+                             g_extra, fine_row_ptr, fine_col, fine_val, g, workspace):
     shift = (ctypes.c_double * 3)(*[float(v) for v in xhat_shift])
     _check(load().agipc_fine_assemble_stvk(
         ctx.handle, int(n_fine), int(tets.shape[0]), _ptr(tets), _ptr(X_rest), _ptr(x), shift, _ptr(E), float(nu),
         _ptr(mass_h2), _ptr(g_extra), _ptr(fine_row_ptr), _ptr(fine_col), int(fine_col.shape[0]), _ptr(fine_val),
-        _ptr(g)), "agipc_fine_assemble_stvk")
+        _ptr(g), _ptr(workspace), 8 * int(workspace.numel())), "agipc_fine_assemble_stvk")
 
 
 def agipc_restrict(ctx: Context, n_fine: int, labels, n_coarse_dev, v, v_c):
@@ -213,10 +221,11 @@ def agipc_restrict(ctx: Context, n_fine: int, labels, n_coarse_dev, v, v_c):
            "agipc_restrict")
 
 
-def agipc_stvk_vjp(ctx: Context, n_fine: int, tets, X_rest, x, E, nu: float, mass_h2, lam, dx, dL_dE, dL_dX_rest):
+def agipc_stvk_vjp(ctx: Context, n_fine: int, tets, X_rest, x, E, nu: float, mass_h2, lam, dx, dL_dE, dL_dX_rest,
+                   workspace):
     _check(load().agipc_stvk_vjp(ctx.handle, int(n_fine), int(tets.shape[0]), _ptr(tets), _ptr(X_rest), _ptr(x),
                                  _ptr(E), float(nu), _ptr(mass_h2), _ptr(lam), _ptr(dx), _ptr(dL_dE),
-                                 _ptr(dL_dX_rest)), "agipc_stvk_vjp")
+                                 _ptr(dL_dX_rest), _ptr(workspace), 8 * int(workspace.numel())), "agipc_stvk_vjp")
 
 
 AGGREGATE_STATIC_MAX_NODES = 1 << 20
@@ -453,6 +462,7 @@ class DiffStep:
         self.adj_relres = torch.zeros(1, **f64)
         self.dL_dE = torch.empty(dp.tets.shape[0], **f64)
         self.dL_dX = torch.empty(n, 3, **f64)
+        self.workspace = stvk_workspace(dp.tets.shape[0], dev)
         self.E = None
         self.X_rest = None
 
@@ -460,7 +470,7 @@ class DiffStep:
         dp, ctx = self.dp, self.ctx
         self.E, self.X_rest = E, X_rest
         agipc_fine_assemble_stvk(ctx, dp.n, dp.tets, X_rest, dp.x, dp.xhat_shift, E, dp.nu, dp.mass_h2, dp.g_extra,
-                                 dp.row_ptr, dp.col, self.fine_val, self.g)
+                                 dp.row_ptr, dp.col, self.fine_val, self.g, self.workspace)
         agipc_aggregate(ctx, dp.n, dp.edges, dp.tags, self.labels, self.n_c)
         agipc_assemble_coarse(ctx, dp.n, self.labels, self.n_c, dp.row_ptr, dp.col, self.fine_val, dp.pair_idx,
                               dp.pair_blk, self.g, self.row_ptr, self.col, self.val, self.nnz, self.g_c, self.dinv)
@@ -478,7 +488,7 @@ class DiffStep:
                   self.adjoint_tol, self.max_iter, 1, self.adj_iters, self.adj_relres)
         agipc_prolongate(ctx, dp.n, self.labels, self.lam_c, self.lam)
         agipc_stvk_vjp(ctx, dp.n, dp.tets, self.X_rest, dp.x, self.E, dp.nu, dp.mass_h2, self.lam, self.dx,
-                       self.dL_dE, self.dL_dX)
+                       self.dL_dE, self.dL_dX, self.workspace)
         return self.dL_dE, self.dL_dX
 
 

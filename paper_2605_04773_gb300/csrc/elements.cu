@@ -9,191 +9,78 @@
 //   agipc_stvk_vjp : the adjoint's per-element contraction.  With the
 //       coarse adjoint lambda_c = H_c^-1 U v (v = dL/dx_next) and
 //       lambda = U^T lambda_c, the step's sensitivity to a parameter theta
-//       is dL/dtheta = -lambda^T (dg/dtheta + dH/dtheta dx).  For the
-//       per-element Young's modulus E_e (Psi_e is linear in E_e at fixed nu
-//       and the eigenvalue clamp commutes with positive scaling) this is
-//       -lambda_e^T (g_e + H_e dx_e) / E_e.  For the rest positions it is the
-//       derivative of phi_e(X) = lambda_e^T g_e(X) + lambda_e^T H_e+(X) dx_e,
-//       where the clamp H+ = V max(L,0) V^T is differentiated through the
-//       eigendecomposition: lambda^T dH+ dx = <dH, V (F o (a b^T)) V^T> with
-//       a = V^T lambda, b = V^T dx and F the divided differences of
-//       max(.,0) over the eigenvalues; dH and dg come from forward-mode dual
-//       numbers, one pass per rest coordinate.  The inertia term M/h^2 (x -
-//       x_hat), x_hat = X_rest + h^2 gravity, adds lambda M/h^2 per vertex.
+//       is dL/dtheta = -lambda^T (dg/dtheta + dH/dtheta dx).  For the rest
+//       positions X this is the derivative of
+//       phi_e(X) = lambda_e^T g_e(X) + lambda_e^T H_e+(X) dx_e, where the
+//       clamp H+ = U max(L,0) U^T is differentiated through the
+//       eigendecomposition (Daleckii-Krein): lambda^T dH+ dx = <dH, Z>,
+//       Z = U (D o (a b^T)) U^T, a = U^T lambda, b = U^T dx, D the divided
+//       differences of max(.,0) over the eigenvalues.  phi_e is then
+//       differentiated in reverse mode, by hand.  For the per-tet Young's
+//       modulus (Psi_e is linear in E_e at fixed nu and the clamp commutes
+//       with positive scaling) dL/dE_e = -phi_e / E_e.  The inertia term
+//       M/h^2 (x - x_hat), x_hat = X_rest + shift, adds lambda M/h^2.
 //
 // Element formulas (independent of the input generator, same physics):
 //   F = Ds Dm^-1, G = (F^T F - I)/2, S = 2 mu G + lam tr(G) I, P = F S,
-//   g[a,c] = V sum_j P[c][j] w[a][j], with w the shape-function gradients
-//   (rows of Dm^-1, w_0 = -sum), and
+//   g[a,c] = V (P w_a)_c with w_a the shape-function gradients (rows of
+//   Dm^-1, w_0 = -sum), and
 //   H[a,c][b,d] = V (delta_cd w_a.S w_b + mu Y_b[c] Y_a[d] + mu (F F^T)_cd
 //                 w_a.w_b + lam Y_a[c] Y_b[d]),  Y_a = F w_a.
-// The 12x12 eigendecomposition is the cyclic Jacobi method (rotation
+//
+// Translations are an exact null space of H, so the spectrum lives in the
+// 9-dimensional complement: with the Helmert basis Q4 (4x3, orthonormal
+// columns orthogonal to (1,1,1,1)) and Q = Q4 (x) I3, H = Q M Q^T where M
+// has the same formula with the three reduced gradients wh_k = sum_a
+// Q4[a][k] w_a in place of the four w_a; H+ = Q M+ Q^T.
+//
+// The projection is computed in two passes.  Every tet's exact Hessian H
+// is summed; a cyclic Jacobi eigendecomposition of M in FP32 (rotation
 // angles by the Rutishauser formulas, Golub & Van Loan, Matrix
-// Computations, Sec. 8.5), run in FP64 by one thread per tet.
+// Computations, Sec. 8.5) then flags the tets whose smallest eigenvalue is
+// not clearly positive (below 1e-4 of the largest, far above FP32's error).
+// Those alone get the FP64 correction -Q M_neg Q^T: the FP32 eigenvectors,
+// re-orthonormalised in FP64, turn M into a nearly diagonal A = U^T M U,
+// FP64 Jacobi sweeps over the pairs that touch the flagged eigenvalues
+// decouple the non-positive block, and M_neg = sum_{A_ii < 0} A_ii u_i u_i^T.
+// Positive-definite tets (about half of a deformed mesh) so skip every FP64
+// eigen step.  The VJP reuses the split: all tets take the unprojected
+// terms (D = 1), flagged tets add the correction of D - 1.
 #include <math.h>
 
 #include "agipc_common.cuh"
 
 namespace {
 
-struct Dual {
-    double v, d;
+constexpr double kR2 = 0.70710678118654752440;   // 1/sqrt(2)
+constexpr double kR6 = 0.40824829046386301637;   // 1/sqrt(6)
+constexpr double kR12 = 0.28867513459481288225;  // 1/sqrt(12)
+
+// Helmert basis of the complement of (1,1,1,1) in R^4.
+__host__ __device__ constexpr double hq(int a, int k)
+{
+    return k == 0 ? (a == 0 ? kR2 : a == 1 ? -kR2 : 0.0)
+         : k == 1 ? (a <= 1 ? kR6 : a == 2 ? -2.0 * kR6 : 0.0)
+                  : (a <= 2 ? kR12 : -3.0 * kR12);
+}
+
+constexpr float kPdRel = 1e-4f;      // "clearly positive" eigenvalue threshold (x largest |eigenvalue|)
+constexpr int kSweeps32 = 10;        // FP32 Jacobi sweep cap
+constexpr int kSweeps64 = 4;         // FP64 refinement sweep cap
+constexpr int kRefineThreads = 32;   // one warp per block in the refinement kernels
+constexpr int kRefineSlots = 189;    // FP64 words of shared memory per refinement thread (48,384 B a block)
+
+struct Tet {
+    double V;           // volume
+    double W[3][3];     // Dm^-1; row k is the shape gradient of vertex k+1
+    double w0[3];       // shape gradient of vertex 0
+    double wh[3][3];    // reduced gradients wh[k] = sum_a hq(a,k) w_a
+    double xh[3][3];    // reduced positions
+    double F[3][3], S[3][3], FFt[3][3];
+    double Y[3][3];     // Y[k] = F wh[k]
+    double s[3][3];     // wh_k . S wh_l
+    double om[3][3];    // wh_k . wh_l
 };
-__device__ __forceinline__ Dual operator+(Dual a, Dual b) { return {a.v + b.v, a.d + b.d}; }
-__device__ __forceinline__ Dual operator-(Dual a, Dual b) { return {a.v - b.v, a.d - b.d}; }
-__device__ __forceinline__ Dual operator-(Dual a) { return {-a.v, -a.d}; }
-__device__ __forceinline__ Dual operator*(Dual a, Dual b) { return {a.v * b.v, a.v * b.d + a.d * b.v}; }
-__device__ __forceinline__ Dual operator*(double s, Dual a) { return {s * a.v, s * a.d}; }
-__device__ __forceinline__ Dual operator*(Dual a, double s) { return {s * a.v, s * a.d}; }
-__device__ __forceinline__ Dual operator-(Dual a, double s) { return {a.v - s, a.d}; }
-__device__ __forceinline__ Dual operator/(Dual a, Dual b)
-{
-    const double q = a.v / b.v;
-    return {q, (a.d - q * b.d) / b.v};
-}
-__device__ __forceinline__ double val(double a) { return a; }
-__device__ __forceinline__ double val(Dual a) { return a.v; }
-template <class S>
-__device__ __forceinline__ S sabs(S a)
-{
-    return val(a) < 0.0 ? -a : a;
-}
-
-// StVK gradient g[12] and (unprojected, symmetric) Hessian H[12][12] of one
-// tet, for rest positions X[4][3] (scalar type S) and positions x[4][3].
-template <class S>
-__device__ void stvk_tet(const S X[4][3], const double x[4][3], double mu, double lam, S g[12], S H[12][12])
-{
-    S Dm[3][3];
-    double Ds[3][3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            Dm[c][k] = X[k + 1][c] - X[0][c];
-            Ds[c][k] = x[k + 1][c] - x[0][c];
-        }
-    const S c00 = Dm[1][1] * Dm[2][2] - Dm[1][2] * Dm[2][1];
-    const S c01 = Dm[1][2] * Dm[2][0] - Dm[1][0] * Dm[2][2];
-    const S c02 = Dm[1][0] * Dm[2][1] - Dm[1][1] * Dm[2][0];
-    const S det = Dm[0][0] * c00 + Dm[0][1] * c01 + Dm[0][2] * c02;
-    S inv[3][3];
-    inv[0][0] = c00 / det;
-    inv[0][1] = (Dm[0][2] * Dm[2][1] - Dm[0][1] * Dm[2][2]) / det;
-    inv[0][2] = (Dm[0][1] * Dm[1][2] - Dm[0][2] * Dm[1][1]) / det;
-    inv[1][0] = c01 / det;
-    inv[1][1] = (Dm[0][0] * Dm[2][2] - Dm[0][2] * Dm[2][0]) / det;
-    inv[1][2] = (Dm[0][2] * Dm[1][0] - Dm[0][0] * Dm[1][2]) / det;
-    inv[2][0] = c02 / det;
-    inv[2][1] = (Dm[0][1] * Dm[2][0] - Dm[0][0] * Dm[2][1]) / det;
-    inv[2][2] = (Dm[0][0] * Dm[1][1] - Dm[0][1] * Dm[1][0]) / det;
-    const S vol = sabs(det) * (1.0 / 6.0);
-    S w[4][3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        w[1][j] = inv[0][j];
-        w[2][j] = inv[1][j];
-        w[3][j] = inv[2][j];
-        w[0][j] = -(inv[0][j] + inv[1][j] + inv[2][j]);
-    }
-    S F[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) F[i][j] = Ds[i][0] * inv[0][j] + Ds[i][1] * inv[1][j] + Ds[i][2] * inv[2][j];
-    S Gm[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            S t = F[0][i] * F[0][j] + F[1][i] * F[1][j] + F[2][i] * F[2][j];
-            Gm[i][j] = 0.5 * (i == j ? t - 1.0 : t);
-        }
-    const S trG = Gm[0][0] + Gm[1][1] + Gm[2][2];
-    S Sm[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) Sm[i][j] = (2.0 * mu) * Gm[i][j] + (i == j ? lam * trG : 0.0 * trG);
-    S P[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) P[i][j] = F[i][0] * Sm[0][j] + F[i][1] * Sm[1][j] + F[i][2] * Sm[2][j];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) g[3 * a + c] = vol * (P[c][0] * w[a][0] + P[c][1] * w[a][1] + P[c][2] * w[a][2]);
-    S FFt[3][3], Y[4][3], Sw[4][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) FFt[i][k] = F[i][0] * F[k][0] + F[i][1] * F[k][1] + F[i][2] * F[k][2];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            Y[a][c] = F[c][0] * w[a][0] + F[c][1] * w[a][1] + F[c][2] * w[a][2];
-            Sw[a][c] = Sm[c][0] * w[a][0] + Sm[c][1] * w[a][1] + Sm[c][2] * w[a][2];
-        }
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const S wSw = w[a][0] * Sw[b][0] + w[a][1] * Sw[b][1] + w[a][2] * Sw[b][2];
-            const S ww = w[a][0] * w[b][0] + w[a][1] * w[b][1] + w[a][2] * w[b][2];
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    S h = mu * (Y[b][c] * Y[a][d]) + mu * (FFt[c][d] * ww) + lam * (Y[a][c] * Y[b][d]);
-                    if (c == d) h = h + wSw;
-                    H[3 * a + c][3 * b + d] = vol * h;
-                }
-        }
-}
-
-// Cyclic Jacobi eigendecomposition of a symmetric 12x12 matrix: A is
-// overwritten (its diagonal ends up holding the eigenvalues), V collects the
-// eigenvectors as columns.
-__device__ void jacobi12(double A[12][12], double V[12][12])
-{
-    for (int i = 0; i < 12; ++i)
-        for (int j = 0; j < 12; ++j) V[i][j] = i == j ? 1.0 : 0.0;
-    double scale = 0.0;
-    for (int i = 0; i < 12; ++i) scale = fmax(scale, fabs(A[i][i]));
-    for (int sweep = 0; sweep < 20; ++sweep) {
-        double off = 0.0;
-        for (int p = 0; p < 12; ++p)
-            for (int q = p + 1; q < 12; ++q) off = fmax(off, fabs(A[p][q]));
-        if (off <= 1e-15 * scale || off == 0.0) break;
-        for (int p = 0; p < 11; ++p)
-            for (int q = p + 1; q < 12; ++q) {
-                const double apq = A[p][q];
-                if (fabs(apq) <= 1e-300) continue;
-                const double theta = (A[q][q] - A[p][p]) / (2.0 * apq);
-                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                const double c = 1.0 / sqrt(t * t + 1.0);
-                const double s = t * c;
-                const double tau = s / (1.0 + c);
-                A[p][p] -= t * apq;
-                A[q][q] += t * apq;
-                A[p][q] = A[q][p] = 0.0;
-                for (int k = 0; k < 12; ++k) {
-                    if (k != p && k != q) {
-                        const double akp = A[k][p], akq = A[k][q];
-                        const double np = akp - s * (akq + tau * akp);
-                        const double nq = akq + s * (akp - tau * akq);
-                        A[k][p] = A[p][k] = np;
-                        A[k][q] = A[q][k] = nq;
-                    }
-                    const double vkp = V[k][p], vkq = V[k][q];
-                    V[k][p] = vkp - s * (vkq + tau * vkp);
-                    V[k][q] = vkq + s * (vkp - tau * vkq);
-                }
-            }
-    }
-}
 
 __device__ __forceinline__ void lame(double E, double nu, double &mu, double &lam)
 {
@@ -201,16 +88,16 @@ __device__ __forceinline__ void lame(double E, double nu, double &mu, double &la
     lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
 }
 
-__device__ __forceinline__ void load_tet(const int32_t *tets, int64_t e, int32_t n, const double *Xr, const double *xc,
-                                         int vid[4], double X[4][3], double x[4][3], bool &ok)
+__device__ __forceinline__ bool load_tet(const int32_t *tets, int64_t e, int32_t n, const double *Xr, const double *xc,
+                                         int vid[4], double X[4][3], double x[4][3])
 {
-    ok = true;
+    bool ok = true;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
         vid[a] = tets[4 * e + a];
         if ((unsigned)vid[a] >= (unsigned)n) ok = false;
     }
-    if (!ok) return;
+    if (!ok) return false;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -218,8 +105,311 @@ __device__ __forceinline__ void load_tet(const int32_t *tets, int64_t e, int32_t
             X[a][c] = Xr[3 * (int64_t)vid[a] + c];
             x[a][c] = xc[3 * (int64_t)vid[a] + c];
         }
+    return true;
 }
 
+__device__ __forceinline__ void tet_eval(const double X[4][3], const double x[4][3], double mu, double lam, Tet &t)
+{
+    double Dm[3][3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) Dm[c][k] = X[k + 1][c] - X[0][c];
+    const double c00 = Dm[1][1] * Dm[2][2] - Dm[1][2] * Dm[2][1];
+    const double c01 = Dm[1][2] * Dm[2][0] - Dm[1][0] * Dm[2][2];
+    const double c02 = Dm[1][0] * Dm[2][1] - Dm[1][1] * Dm[2][0];
+    const double det = Dm[0][0] * c00 + Dm[0][1] * c01 + Dm[0][2] * c02;
+    const double id = 1.0 / det;
+    t.W[0][0] = c00 * id;
+    t.W[0][1] = (Dm[0][2] * Dm[2][1] - Dm[0][1] * Dm[2][2]) * id;
+    t.W[0][2] = (Dm[0][1] * Dm[1][2] - Dm[0][2] * Dm[1][1]) * id;
+    t.W[1][0] = c01 * id;
+    t.W[1][1] = (Dm[0][0] * Dm[2][2] - Dm[0][2] * Dm[2][0]) * id;
+    t.W[1][2] = (Dm[0][2] * Dm[1][0] - Dm[0][0] * Dm[1][2]) * id;
+    t.W[2][0] = c02 * id;
+    t.W[2][1] = (Dm[0][1] * Dm[2][0] - Dm[0][0] * Dm[2][1]) * id;
+    t.W[2][2] = (Dm[0][0] * Dm[1][1] - Dm[0][1] * Dm[1][0]) * id;
+    t.V = fabs(det) * (1.0 / 6.0);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) t.w0[j] = -(t.W[0][j] + t.W[1][j] + t.W[2][j]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            double v = hq(0, k) * t.w0[j];
+#pragma unroll
+            for (int a = 1; a < 4; ++a) v += hq(a, k) * t.W[a - 1][j];
+            t.wh[k][j] = v;
+            double u = 0.0;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) u += hq(a, k) * x[a][j];
+            t.xh[k][j] = u;
+        }
+    // F = sum_a x_a w_a^T = sum_k xh_k wh_k^T
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            t.F[i][j] = t.xh[0][i] * t.wh[0][j] + t.xh[1][i] * t.wh[1][j] + t.xh[2][i] * t.wh[2][j];
+    double G[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const double v = t.F[0][i] * t.F[0][j] + t.F[1][i] * t.F[1][j] + t.F[2][i] * t.F[2][j];
+            G[i][j] = 0.5 * (i == j ? v - 1.0 : v);
+        }
+    const double trG = G[0][0] + G[1][1] + G[2][2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            t.S[i][j] = 2.0 * mu * G[i][j] + (i == j ? lam * trG : 0.0);
+            t.FFt[i][j] = t.F[i][0] * t.F[j][0] + t.F[i][1] * t.F[j][1] + t.F[i][2] * t.F[j][2];
+        }
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            t.Y[k][c] = t.F[c][0] * t.wh[k][0] + t.F[c][1] * t.wh[k][1] + t.F[c][2] * t.wh[k][2];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+            double sv = 0.0, ov = 0.0;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const double Swl = t.S[i][0] * t.wh[l][0] + t.S[i][1] * t.wh[l][1] + t.S[i][2] * t.wh[l][2];
+                sv += t.wh[k][i] * Swl;
+                ov += t.wh[k][i] * t.wh[l][i];
+            }
+            t.s[k][l] = sv;
+            t.om[k][l] = ov;
+        }
+}
+
+// Shape gradient of vertex a.
+__device__ __forceinline__ double wgrad(const Tet &t, int a, int j) { return a == 0 ? t.w0[j] : t.W[a - 1][j]; }
+
+// Packed upper-triangle index of a symmetric 9x9 matrix.
+__host__ __device__ constexpr int pk(int i, int j)
+{
+    return i <= j ? 9 * i - (i * (i - 1)) / 2 + (j - i) : 9 * j - (j * (j - 1)) / 2 + (i - j);
+}
+
+// Reduced Hessian M (9x9, index 3k+c), FP32, packed upper.
+__device__ __forceinline__ void reduced_m32(const Tet &t, double mu, double lam, float A[45])
+{
+#pragma unroll
+    for (int r = 0; r < 9; ++r)
+#pragma unroll
+        for (int q = r; q < 9; ++q) {
+            const int k = r / 3, c = r % 3, l = q / 3, d = q % 3;
+            double v = mu * t.Y[l][c] * t.Y[k][d] + mu * t.FFt[c][d] * t.om[k][l] + lam * t.Y[k][c] * t.Y[l][d];
+            if (c == d) v += t.s[k][l];
+            A[pk(r, q)] = (float)(t.V * v);
+        }
+}
+
+// out = M v for the reduced Hessian, FP64, matrix-free.
+__device__ __forceinline__ void reduced_mv(const Tet &t, double mu, double lam, const double v[9], double out[9])
+{
+    double Fv[3][3], Yv[3], YkVl[3][3];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            Fv[l][c] = t.FFt[c][0] * v[3 * l] + t.FFt[c][1] * v[3 * l + 1] + t.FFt[c][2] * v[3 * l + 2];
+        Yv[l] = t.Y[l][0] * v[3 * l] + t.Y[l][1] * v[3 * l + 1] + t.Y[l][2] * v[3 * l + 2];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            YkVl[k][l] = t.Y[k][0] * v[3 * l] + t.Y[k][1] * v[3 * l + 1] + t.Y[k][2] * v[3 * l + 2];
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            double acc = 0.0;
+#pragma unroll
+            for (int l = 0; l < 3; ++l)
+                acc += t.s[k][l] * v[3 * l + c] + mu * t.Y[l][c] * YkVl[k][l] + mu * t.om[k][l] * Fv[l][c] +
+                       lam * t.Y[k][c] * Yv[l];
+            out[3 * k + c] = t.V * acc;
+        }
+}
+
+// Cyclic Jacobi on a packed symmetric 9x9 FP32 matrix: A becomes (nearly)
+// diagonal, U collects the eigenvectors as columns.  Branch-free rotations;
+// the warp leaves the sweep loop when all its lanes have converged.
+__device__ __forceinline__ void jacobi9f(float A[45], float U[9][9])
+{
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+#pragma unroll
+        for (int j = 0; j < 9; ++j) U[i][j] = i == j ? 1.f : 0.f;
+    float fro = 0.f;
+#pragma unroll
+    for (int r = 0; r < 9; ++r)
+#pragma unroll
+        for (int q = r; q < 9; ++q) fro += (r == q ? 1.f : 2.f) * A[pk(r, q)] * A[pk(r, q)];
+    const float scale = sqrtf(fro);
+    const float thr = 1e-9f * scale;
+    for (int sweep = 0; sweep < kSweeps32; ++sweep) {
+        float off = 0.f;
+#pragma unroll
+        for (int p = 0; p < 9; ++p)
+#pragma unroll
+            for (int q = p + 1; q < 9; ++q) off = fmaxf(off, fabsf(A[pk(p, q)]));
+        if (__all_sync(__activemask(), !(off > 1e-6f * scale))) break;
+#pragma unroll
+        for (int p = 0; p < 8; ++p)
+#pragma unroll
+            for (int q = p + 1; q < 9; ++q) {
+                const float apq = A[pk(p, q)];
+                const bool rot = fabsf(apq) > thr;
+                const float theta = (A[pk(q, q)] - A[pk(p, p)]) / (2.f * (rot ? apq : 1.f));
+                float tt = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
+                tt = rot ? tt : 0.f;
+                const float c = rsqrtf(tt * tt + 1.f);
+                const float s = tt * c;
+                const float tau = s / (1.f + c);
+                A[pk(p, p)] -= tt * apq;
+                A[pk(q, q)] += tt * apq;
+                A[pk(p, q)] = rot ? 0.f : apq;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    if (k != p && k != q) {
+                        const float akp = A[pk(k, p)], akq = A[pk(k, q)];
+                        A[pk(k, p)] = akp - s * (akq + tau * akp);
+                        A[pk(k, q)] = akq + s * (akp - tau * akq);
+                    }
+                    const float ukp = U[k][p], ukq = U[k][q];
+                    U[k][p] = ukp - s * (ukq + tau * ukp);
+                    U[k][q] = ukq + s * (ukp - tau * ukq);
+                }
+            }
+    }
+}
+
+// FP32 eigen-classification of a tet's reduced Hessian: the number of
+// eigenvalues that are not clearly positive.
+__device__ __forceinline__ int flagged_count(const float A[45])
+{
+    float big = 0.f;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) big = fmaxf(big, fabsf(A[pk(i, i)]));
+    int m = 0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) m += A[pk(i, i)] <= kPdRel * big ? 1 : 0;
+    return m;
+}
+
+// Shared-memory slots of one refinement thread: U (81 words, column j at
+// 9j), then A (45 words, packed upper), then room for 12 x 9 words of
+// Q-expanded eigenvectors that may overwrite A once it has been read.  Slot
+// s of thread `lane` lives at sm[s * kRefineThreads + lane] so that a
+// warp's accesses hit 32 banks.
+struct Slots {
+    double *base;
+    int lane;
+    __device__ __forceinline__ double &u(int row, int col) const { return base[(9 * col + row) * kRefineThreads + lane]; }
+    __device__ __forceinline__ double &a(int i, int j) const { return base[(81 + pk(i, j)) * kRefineThreads + lane]; }
+    __device__ __forceinline__ double &raw(int s) const { return base[s * kRefineThreads + lane]; }
+};
+
+// FP64 refinement of a tet's FP32 eigenbasis.  Recomputes the FP32
+// decomposition, orders the flagged eigenvalues first, re-orthonormalises
+// U in FP64 (modified Gram-Schmidt), forms A = U^T M U and runs FP64
+// Jacobi sweeps over every pair (p, q) with p < m_warp (all pairs when
+// all_pairs), m_warp the warp's largest flagged count.  Returns m_warp.
+__device__ int refine64(const Tet &t, double mu, double lam, const Slots &sl, bool all_pairs)
+{
+    float A32[45], U32[9][9];
+    reduced_m32(t, mu, lam, A32);
+    jacobi9f(A32, U32);
+    float big = 0.f;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) big = fmaxf(big, fabsf(A32[pk(i, i)]));
+    // order: flagged eigenvalues first (stable in index), then the rest
+    int nf = 0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) nf += A32[pk(i, i)] <= kPdRel * big ? 1 : 0;
+    int fi = 0, pi = nf;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const bool f = A32[pk(i, i)] <= kPdRel * big;
+        const int slot = f ? fi : pi;
+        fi += f ? 1 : 0;
+        pi += f ? 0 : 1;
+#pragma unroll
+        for (int r = 0; r < 9; ++r) sl.u(r, slot) = (double)U32[r][i];
+    }
+    const unsigned mask = __activemask();
+    const int m_warp = all_pairs ? 8 : __reduce_max_sync(mask, nf);
+    // modified Gram-Schmidt in FP64
+    for (int j = 0; j < 9; ++j) {
+        for (int i = 0; i < j; ++i) {
+            double d = 0.0;
+#pragma unroll
+            for (int r = 0; r < 9; ++r) d += sl.u(r, i) * sl.u(r, j);
+#pragma unroll
+            for (int r = 0; r < 9; ++r) sl.u(r, j) -= d * sl.u(r, i);
+        }
+        double nrm = 0.0;
+#pragma unroll
+        for (int r = 0; r < 9; ++r) nrm += sl.u(r, j) * sl.u(r, j);
+        const double inv = 1.0 / sqrt(nrm);
+#pragma unroll
+        for (int r = 0; r < 9; ++r) sl.u(r, j) *= inv;
+    }
+    // A = U^T M U
+    double scale = 0.0;
+    for (int j = 0; j < 9; ++j) {
+        double v[9], mv[9];
+#pragma unroll
+        for (int r = 0; r < 9; ++r) v[r] = sl.u(r, j);
+        reduced_mv(t, mu, lam, v, mv);
+        for (int i = 0; i <= j; ++i) {
+            double d = 0.0;
+#pragma unroll
+            for (int r = 0; r < 9; ++r) d += sl.u(r, i) * mv[r];
+            sl.a(i, j) = d;
+            scale = fmax(scale, fabs(d));
+        }
+    }
+    const double thr = 1e-300;
+    for (int sweep = 0; sweep < kSweeps64; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < m_warp; ++p)
+            for (int q = p + 1; q < 9; ++q) off = fmax(off, fabs(sl.a(p, q)));
+        if (__all_sync(mask, !(off > 1e-15 * scale))) break;
+        for (int p = 0; p < m_warp; ++p)
+            for (int q = p + 1; q < 9; ++q) {
+                const double apq = sl.a(p, q);
+                const bool rot = fabs(apq) > thr;
+                const double theta = (sl.a(q, q) - sl.a(p, p)) / (2.0 * (rot ? apq : 1.0));
+                double tt = copysign(1.0, theta) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                tt = rot ? tt : 0.0;
+                const double c = 1.0 / sqrt(tt * tt + 1.0);
+                const double s = tt * c;
+                const double tau = s / (1.0 + c);
+                sl.a(p, p) -= tt * apq;
+                sl.a(q, q) += tt * apq;
+                sl.a(p, q) = rot ? 0.0 : apq;
+                for (int k = 0; k < 9; ++k) {
+                    if (k != p && k != q) {
+                        const double akp = sl.a(k, p), akq = sl.a(k, q);
+                        sl.a(k, p) = akp - s * (akq + tau * akp);
+                        sl.a(k, q) = akq + s * (akp - tau * akq);
+                    }
+                    const double ukp = sl.u(k, p), ukq = sl.u(k, q);
+                    sl.u(k, p) = ukp - s * (ukq + tau * ukp);
+                    sl.u(k, q) = ukq + s * (ukp - tau * ukq);
+                }
+            }
+    }
+    return m_warp;
+}
 
 // Position of block (r, c), r <= c, in the sorted columns of row r; -1 if the
 // structure lacks it.
@@ -236,6 +426,54 @@ __device__ __forceinline__ int64_t find_block(const int32_t *__restrict__ row_pt
         else hi = mid - 1;
     }
     return -1;
+}
+
+// Local vertex pairs (s, t), s <= t, of the 10 upper 3x3 blocks of a tet.
+__host__ __device__ constexpr int pair_s(int q) { return q < 4 ? 0 : q < 7 ? 1 : q < 9 ? 2 : 3; }
+__host__ __device__ constexpr int pair_t(int q) { return q < 4 ? q : q < 7 ? q - 3 : q < 9 ? q - 5 : 3; }
+
+// Adds blk(c, d) to the fine block of local vertex pair (sa, sb); reports a
+// missing block.
+template <class Blk>
+__device__ __forceinline__ void scatter_block(const int32_t *row_ptr, const int32_t *col, int64_t nnzb,
+                                              double *fine_val, const int vid[4], int sa, int sb, Blk blk,
+                                              uint32_t *status)
+{
+    const int32_t va = vid[sa], vb = vid[sb];
+    if (sa != sb && va == vb) {
+        set_status(status, ST_BAD_INDEX);
+        return;
+    }
+    const bool tr = va > vb;
+    const int64_t pos = find_block(row_ptr, col, nnzb, tr ? vb : va, tr ? va : vb);
+    if (pos < 0) {
+        set_status(status, ST_BAD_INDEX);
+        return;
+    }
+    double *dst = fine_val + 9 * pos;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) atomicAdd(dst + (tr ? 3 * d + c : 3 * c + d), blk(c, d));
+}
+
+// Warp-aggregated append to the flagged-tet list.
+__device__ __forceinline__ void enqueue(int32_t *list_count, int32_t *list, int64_t cap, int32_t e, bool flag,
+                                        uint32_t *status)
+{
+    const unsigned mask = __activemask();
+    const unsigned ballot = __ballot_sync(mask, flag);
+    if (!ballot) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(ballot) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(list_count, __popc(ballot));
+    base = __shfl_sync(mask, base, leader);
+    if (flag) {
+        const int64_t at = base + __popc(ballot & ((1u << lane) - 1u));
+        if (at < cap) list[at] = e;
+        else set_status(status, ST_CAPACITY);
+    }
 }
 
 struct Shift3 {
@@ -269,150 +507,435 @@ __global__ void fine_init_kernel(int32_t n, const int32_t *__restrict__ row_ptr,
     }
 }
 
-__constant__ int kPairS[10] = {0, 0, 0, 0, 1, 1, 1, 2, 2, 3};
-__constant__ int kPairT[10] = {0, 1, 2, 3, 1, 2, 3, 2, 3, 3};
-
-__global__ void __launch_bounds__(128) elem_assemble_kernel(int32_t n, int64_t nt, const int32_t *__restrict__ tets,
-                                                            const int32_t *__restrict__ row_ptr,
-                                                            const int32_t *__restrict__ col, int64_t nnzb,
-                                                            const double *__restrict__ Xr, const double *__restrict__ xc,
-                                                            const double *__restrict__ E, double nu, double *fine_val,
-                                                            double *g, uint32_t *status)
+// Pass 1 of the assembly, one thread per tet: gradient and exact Hessian
+// blocks in FP64, FP32 eigen-classification, flagged tets to the list.
+__global__ void __launch_bounds__(128) elem_pass1_kernel(int32_t n, int64_t nt, const int32_t *__restrict__ tets,
+                                                         const int32_t *__restrict__ row_ptr,
+                                                         const int32_t *__restrict__ col, int64_t nnzb,
+                                                         const double *__restrict__ Xr, const double *__restrict__ xc,
+                                                         const double *__restrict__ E, double nu, double *fine_val,
+                                                         double *g, int32_t *list_count, int32_t *list,
+                                                         uint32_t *status)
 {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nt; e += (int64_t)gridDim.x * blockDim.x) {
         int vid[4];
         double X[4][3], x[4][3];
-        bool ok;
-        load_tet(tets, e, n, Xr, xc, vid, X, x, ok);
-        if (!ok) {
+        bool flag = false;
+        if (!load_tet(tets, e, n, Xr, xc, vid, X, x)) {
             set_status(status, ST_BAD_INDEX);
-            continue;
-        }
-        double mu, lam;
-        lame(E[e], nu, mu, lam);
-        double ge[12], H[12][12], V[12][12];
-        stvk_tet<double>(X, x, mu, lam, ge, H);
-        bool finite = true;
-        for (int r = 0; r < 12; ++r) finite = finite && isfinite(ge[r]);
-        if (!finite) {
-            set_status(status, ST_NONFINITE);
-            continue;
-        }
-        // PSD projection: H+ = V max(L, 0) V^T
-        jacobi12(H, V);
-        double L[12];
-        for (int k = 0; k < 12; ++k) L[k] = fmax(H[k][k], 0.0);
-        for (int q = 0; q < 10; ++q) {
-            const int sa = kPairS[q], sb = kPairT[q];
-            const int32_t va = vid[sa], vb = vid[sb];
-            if (sa != sb && va == vb) {
-                set_status(status, ST_BAD_INDEX);
-                continue;
-            }
-            const bool transpose = va > vb;
-            const int64_t pos = find_block(row_ptr, col, nnzb, transpose ? vb : va, transpose ? va : vb);
-            if (pos < 0) {
-                set_status(status, ST_BAD_INDEX);
-                continue;
-            }
-            double *dst = fine_val + 9 * pos;
-            for (int c = 0; c < 3; ++c)
-                for (int d = 0; d < 3; ++d) {
-                    const int r = 3 * sa + c, s = 3 * sb + d;
-                    double h = 0.0;
-                    for (int k = 0; k < 12; ++k) h += V[r][k] * L[k] * V[s][k];
-                    atomicAdd(dst + (transpose ? 3 * d + c : 3 * c + d), h);
+        } else {
+            double mu, lam;
+            lame(E[e], nu, mu, lam);
+            Tet t;
+            tet_eval(X, x, mu, lam, t);
+            double P[3][3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) P[i][j] = t.F[i][0] * t.S[0][j] + t.F[i][1] * t.S[1][j] + t.F[i][2] * t.S[2][j];
+            bool finite = isfinite(t.V) && t.V > 0.0;
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const double ga =
+                        t.V * (P[c][0] * wgrad(t, a, 0) + P[c][1] * wgrad(t, a, 1) + P[c][2] * wgrad(t, a, 2));
+                    finite = finite && isfinite(ga);
+                    atomicAdd(g + 3 * (int64_t)vid[a] + c, ga);
                 }
+            if (!finite) {
+                set_status(status, ST_NONFINITE);
+            } else {
+                double Yf[4][3], Sw[4][3];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        Yf[a][c] = t.F[c][0] * wgrad(t, a, 0) + t.F[c][1] * wgrad(t, a, 1) + t.F[c][2] * wgrad(t, a, 2);
+                        Sw[a][c] = t.S[c][0] * wgrad(t, a, 0) + t.S[c][1] * wgrad(t, a, 1) + t.S[c][2] * wgrad(t, a, 2);
+                    }
+#pragma unroll
+                for (int q = 0; q < 10; ++q) {
+                    const int sa = pair_s(q), sb = pair_t(q);
+                    double wSw = 0.0, ww = 0.0;
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        wSw += wgrad(t, sa, j) * Sw[sb][j];
+                        ww += wgrad(t, sa, j) * wgrad(t, sb, j);
+                    }
+                    scatter_block(row_ptr, col, nnzb, fine_val, vid, sa, sb,
+                                  [&](int c, int d) {
+                                      double h = mu * Yf[sb][c] * Yf[sa][d] + mu * t.FFt[c][d] * ww +
+                                                 lam * Yf[sa][c] * Yf[sb][d];
+                                      if (c == d) h += wSw;
+                                      return t.V * h;
+                                  },
+                                  status);
+                }
+                float A32[45], U32[9][9];
+                reduced_m32(t, mu, lam, A32);
+                jacobi9f(A32, U32);
+                flag = flagged_count(A32) > 0;
+            }
         }
-        for (int a = 0; a < 4; ++a)
-            for (int c = 0; c < 3; ++c) atomicAdd(g + 3 * (int64_t)vid[a] + c, ge[3 * a + c]);
+        enqueue(list_count, list, nt, (int32_t)e, flag, status);
     }
 }
 
-__global__ void __launch_bounds__(128) vjp_kernel(int32_t n, int64_t nt, const int32_t *__restrict__ tets,
-                                                  const double *__restrict__ Xr, const double *__restrict__ xc,
-                                                  const double *__restrict__ E, double nu,
-                                                  const double *__restrict__ lam_f, const double *__restrict__ dx,
-                                                  double *__restrict__ dL_dE, double *dL_dX, uint32_t *status)
+// Pass 2 of the assembly, flagged tets only: H+ = H - Q M_neg Q^T.
+__global__ void __launch_bounds__(kRefineThreads) elem_pass2_kernel(
+    int32_t n, const int32_t *__restrict__ tets, const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+    int64_t nnzb, const double *__restrict__ Xr, const double *__restrict__ xc, const double *__restrict__ E, double nu,
+    double *fine_val, const int32_t *__restrict__ list_count, const int32_t *__restrict__ list, int64_t cap,
+    uint32_t *status)
+{
+    __shared__ double sm[kRefineSlots * kRefineThreads];
+    const Slots sl{sm, (int)threadIdx.x};
+    const int64_t cnt = min64((int64_t)*list_count, cap);
+    for (int64_t i = blockIdx.x * (int64_t)kRefineThreads + threadIdx.x; i < cnt;
+         i += (int64_t)gridDim.x * kRefineThreads) {
+        const int64_t e = list[i];
+        int vid[4];
+        double X[4][3], x[4][3];
+        if (!load_tet(tets, e, n, Xr, xc, vid, X, x)) continue;   // reported by pass 1
+        double mu, lam;
+        lame(E[e], nu, mu, lam);
+        Tet t;
+        tet_eval(X, x, mu, lam, t);
+        const int m_w = refine64(t, mu, lam, sl, false);
+        // negative part of the flagged block, then R_i = Q u_i into the
+        // slots from 81 on (A is dead once d is read; U stays intact)
+        double d[9];
+        for (int i2 = 0; i2 < 9; ++i2) {
+            const double aii = i2 < m_w ? sl.a(i2, i2) : 0.0;
+            d[i2] = aii < 0.0 ? aii : 0.0;
+        }
+        for (int i2 = 0; i2 < m_w; ++i2) {
+            double u[9];
+#pragma unroll
+            for (int r = 0; r < 9; ++r) u[r] = sl.u(r, i2);
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    sl.raw(81 + 12 * i2 + 3 * a + c) = hq(a, 0) * u[c] + hq(a, 1) * u[3 + c] + hq(a, 2) * u[6 + c];
+        }
+#pragma unroll
+        for (int q = 0; q < 10; ++q) {
+            const int sa = pair_s(q), sb = pair_t(q);
+            scatter_block(row_ptr, col, nnzb, fine_val, vid, sa, sb,
+                          [&](int c, int dd) {
+                              double acc = 0.0;
+                              for (int i2 = 0; i2 < m_w; ++i2)
+                                  acc += d[i2] * sl.raw(81 + 12 * i2 + 3 * sa + c) * sl.raw(81 + 12 * i2 + 3 * sb + dd);
+                              return -acc;
+                          },
+                          status);
+        }
+    }
+}
+
+// Reverse-mode derivative of psi = <P, Lam> + <Z, Mhat> with respect to the
+// rest positions (Mhat = M / V; Z given entrywise by z(r, q), r = 3k+c).
+// Returns psi and adds dphi/dX (phi = V psi) to Xb.
+template <class ZF>
+__device__ __forceinline__ double reverse_phi(const Tet &t, double mu, double lam, const double lh[3][3],
+                                              bool with_lambda, ZF z, double Xb[4][3])
+{
+    double Fb[3][3], whb[3][3], Yb[3][3];
+    double zt[3][3], R[3][3], rho[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Fb[i][j] = whb[i][j] = Yb[i][j] = zt[i][j] = R[i][j] = rho[i][j] = 0.0;
+    double psi = 0.0;
+    // Z terms: psi35 = sum z (lam Y_k[c] Y_l[d] + mu Y_k[d] Y_l[c]); traces, R, rho
+#pragma unroll
+    for (int r = 0; r < 9; ++r)
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const int k = r / 3, c = r % 3, l = q / 3, d = q % 3;
+            const double zz = z(r, q);
+            psi += zz * (lam * t.Y[k][c] * t.Y[l][d] + mu * t.Y[k][d] * t.Y[l][c]);
+            Yb[k][c] += lam * zz * t.Y[l][d];
+            Yb[l][d] += lam * zz * t.Y[k][c];
+            Yb[k][d] += mu * zz * t.Y[l][c];
+            Yb[l][c] += mu * zz * t.Y[k][d];
+            if (c == d) zt[k][l] += zz;
+            R[c][d] += t.om[k][l] * zz;
+            rho[k][l] += t.FFt[c][d] * zz;
+        }
+    // psi2 = <S, T>, T = sum_kl zt_kl wh_k wh_l^T; psi4 = mu <FFt, R>
+    double T[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            double v = 0.0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+                for (int l = 0; l < 3; ++l) v += zt[k][l] * t.wh[k][i] * t.wh[l][j];
+            T[i][j] = v;
+        }
+    const double trT = T[0][0] + T[1][1] + T[2][2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) psi += t.S[i][j] * T[i][j] + mu * t.FFt[i][j] * R[i][j];
+    // Fbar from psi2: F (2 mu sym(T) + lam tr(T) I); from psi4: mu (R + R^T) F
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            double v = 0.0;
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                const double Tsym = mu * (T[m][j] + T[j][m]) + (m == j ? lam * trT : 0.0);
+                v += t.F[i][m] * Tsym + mu * (R[i][m] + R[m][i]) * t.F[m][j];
+            }
+            Fb[i][j] += v;
+        }
+    // Fbar and whbar from psi35 through Y_k = F wh_k
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                Fb[i][j] += Yb[k][i] * t.wh[k][j];
+                whb[k][j] += t.F[i][j] * Yb[k][i];
+            }
+    // whbar from psi2 (explicit wh) and psi4 (omega)
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+            const double cz = zt[k][l] + zt[l][k];
+            const double cr = mu * (rho[k][l] + rho[l][k]);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const double Swl = t.S[j][0] * t.wh[l][0] + t.S[j][1] * t.wh[l][1] + t.S[j][2] * t.wh[l][2];
+                whb[k][j] += cz * Swl + cr * t.wh[l][j];
+            }
+        }
+    if (with_lambda) {
+        // psi1 = <P, Lam>, Lam = sum_k lh_k wh_k^T
+        double P[3][3], Lam[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                P[i][j] = t.F[i][0] * t.S[0][j] + t.F[i][1] * t.S[1][j] + t.F[i][2] * t.S[2][j];
+                Lam[i][j] = lh[0][i] * t.wh[0][j] + lh[1][i] * t.wh[1][j] + lh[2][i] * t.wh[2][j];
+            }
+        double LF = 0.0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                psi += P[i][j] * Lam[i][j];
+                LF += Lam[i][j] * t.F[i][j];
+            }
+        // Fbar += Lam S + mu F Lam^T F + mu FFt Lam + lam <Lam, F> F
+        double FLt[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                FLt[i][j] = t.F[i][0] * Lam[j][0] + t.F[i][1] * Lam[j][1] + t.F[i][2] * Lam[j][2];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                double v = lam * LF * t.F[i][j];
+#pragma unroll
+                for (int m = 0; m < 3; ++m)
+                    v += Lam[i][m] * t.S[m][j] + mu * FLt[i][m] * t.F[m][j] + mu * t.FFt[i][m] * Lam[m][j];
+                Fb[i][j] += v;
+            }
+        // whbar_k += P^T lh_k
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) whb[k][j] += P[0][j] * lh[k][0] + P[1][j] * lh[k][1] + P[2][j] * lh[k][2];
+    }
+    // F = sum_k xh_k wh_k^T: whbar_k += Fbar^T xh_k
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) whb[k][j] += Fb[0][j] * t.xh[k][0] + Fb[1][j] * t.xh[k][1] + Fb[2][j] * t.xh[k][2];
+    // phi = V psi: wbar_a = V sum_k hq(a,k) whbar_k; Wbar[a-1] = wbar_a - wbar_0
+    double Wb[3][3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const double wb0 = t.V * (hq(0, 0) * whb[0][j] + hq(0, 1) * whb[1][j] + hq(0, 2) * whb[2][j]);
+#pragma unroll
+        for (int a = 1; a < 4; ++a)
+            Wb[a - 1][j] = t.V * (hq(a, 0) * whb[0][j] + hq(a, 1) * whb[1][j] + hq(a, 2) * whb[2][j]) - wb0;
+    }
+    // Dmbar = -W^T Wbar W^T + psi V W^T
+    double WtWb[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) WtWb[i][j] = t.W[0][i] * Wb[0][j] + t.W[1][i] * Wb[1][j] + t.W[2][i] * Wb[2][j];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const double Dmb = -(WtWb[c][0] * t.W[k][0] + WtWb[c][1] * t.W[k][1] + WtWb[c][2] * t.W[k][2]) +
+                               psi * t.V * t.W[k][c];
+            Xb[k + 1][c] += Dmb;
+            Xb[0][c] -= Dmb;
+        }
+    return psi;
+}
+
+__device__ __forceinline__ void reduce_vec(const double v[4][3], double vh[3][3])
+{
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            vh[k][c] = hq(0, k) * v[0][c] + hq(1, k) * v[1][c] + hq(2, k) * v[2][c] + hq(3, k) * v[3][c];
+}
+
+__device__ __forceinline__ void load_pair(const int vid[4], const double *lam_f, const double *dx, double lh[3][3],
+                                          double dh[3][3])
+{
+    double lv[4][3], dv[4][3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            lv[a][c] = lam_f[3 * (int64_t)vid[a] + c];
+            dv[a][c] = dx[3 * (int64_t)vid[a] + c];
+        }
+    reduce_vec(lv, lh);
+    reduce_vec(dv, dh);
+}
+
+// VJP pass 1, one thread per tet: the unprojected terms (D = 1, Z = lh dh^T),
+// dL/dE written, dL/dX accumulated, flagged tets to the list.
+__global__ void __launch_bounds__(128) vjp_pass1_kernel(int32_t n, int64_t nt, const int32_t *__restrict__ tets,
+                                                        const double *__restrict__ Xr, const double *__restrict__ xc,
+                                                        const double *__restrict__ E, double nu,
+                                                        const double *__restrict__ lam_f, const double *__restrict__ dx,
+                                                        double *__restrict__ dL_dE, double *dL_dX,
+                                                        int32_t *list_count, int32_t *list, uint32_t *status)
 {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nt; e += (int64_t)gridDim.x * blockDim.x) {
         int vid[4];
         double X[4][3], x[4][3];
-        bool ok;
-        load_tet(tets, e, n, Xr, xc, vid, X, x, ok);
-        if (!ok) {
+        bool flag = false;
+        if (!load_tet(tets, e, n, Xr, xc, vid, X, x)) {
             set_status(status, ST_BAD_INDEX);
             dL_dE[e] = 0.0;
-            continue;
+        } else {
+            double lh[3][3], dh[3][3];
+            load_pair(vid, lam_f, dx, lh, dh);
+            const double Ee = E[e];
+            double mu, lam;
+            lame(Ee, nu, mu, lam);
+            Tet t;
+            tet_eval(X, x, mu, lam, t);
+            double Xb[4][3] = {};
+            const double psi = reverse_phi(t, mu, lam, lh, true,
+                                           [&](int r, int q) { return lh[r / 3][r % 3] * dh[q / 3][q % 3]; }, Xb);
+            dL_dE[e] = -t.V * psi / Ee;
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) atomicAdd(dL_dX + 3 * (int64_t)vid[a] + c, -Xb[a][c]);
+            float A32[45], U32[9][9];
+            reduced_m32(t, mu, lam, A32);
+            jacobi9f(A32, U32);
+            flag = flagged_count(A32) > 0;
         }
-        double lv[12], dv[12];
-        for (int a = 0; a < 4; ++a)
-            for (int c = 0; c < 3; ++c) {
-                lv[3 * a + c] = lam_f[3 * (int64_t)vid[a] + c];
-                dv[3 * a + c] = dx[3 * (int64_t)vid[a] + c];
-            }
+        enqueue(list_count, list, nt, (int32_t)e, flag, status);
+    }
+}
+
+// (D - 1)_ij, D the divided differences of max(., 0): 0 when both
+// eigenvalues are positive, -1 when neither is, and min/(max - min)
+// otherwise.  Selects only (no divergent branches).
+__device__ __forceinline__ double dd_minus_one(double li, double lj)
+{
+    const bool pi = li > 0.0, pj = lj > 0.0;
+    const double lo = fmin(li, lj), hi = fmax(li, lj);
+    const double mixed = lo / (hi - lo);
+    return pi == pj ? (pi ? 0.0 : -1.0) : mixed;
+}
+
+// VJP pass 2, flagged tets only: the clamp's correction Z = U ((D - 1) o
+// (a b^T)) U^T in the refined eigenbasis (every pair rotated).
+__global__ void __launch_bounds__(kRefineThreads) vjp_pass2_kernel(
+    int32_t n, const int32_t *__restrict__ tets, const double *__restrict__ Xr, const double *__restrict__ xc,
+    const double *__restrict__ E, double nu, const double *__restrict__ lam_f, const double *__restrict__ dx,
+    double *__restrict__ dL_dE, double *dL_dX, const int32_t *__restrict__ list_count,
+    const int32_t *__restrict__ list, int64_t cap)
+{
+    __shared__ double sm[kRefineSlots * kRefineThreads];
+    const Slots sl{sm, (int)threadIdx.x};
+    const int64_t cnt = min64((int64_t)*list_count, cap);
+    for (int64_t i = blockIdx.x * (int64_t)kRefineThreads + threadIdx.x; i < cnt;
+         i += (int64_t)gridDim.x * kRefineThreads) {
+        const int64_t e = list[i];
+        int vid[4];
+        double X[4][3], x[4][3];
+        if (!load_tet(tets, e, n, Xr, xc, vid, X, x)) continue;
+        double lh[3][3], dh[3][3];
+        load_pair(vid, lam_f, dx, lh, dh);
         const double Ee = E[e];
         double mu, lam;
         lame(Ee, nu, mu, lam);
-        double ge[12], H[12][12], V[12][12];
-        stvk_tet<double>(X, x, mu, lam, ge, H);
-        jacobi12(H, V);
-        double Lm[12], a_[12], b_[12];
-        for (int k = 0; k < 12; ++k) {
-            Lm[k] = H[k][k];
+        Tet t;
+        tet_eval(X, x, mu, lam, t);
+        refine64(t, mu, lam, sl, true);
+        double L[9], av[9], bv[9];
+        for (int j = 0; j < 9; ++j) {
+            L[j] = sl.a(j, j);
             double sa = 0.0, sb = 0.0;
-            for (int r = 0; r < 12; ++r) {
-                sa += V[r][k] * lv[r];
-                sb += V[r][k] * dv[r];
+#pragma unroll
+            for (int r = 0; r < 9; ++r) {
+                sa += sl.u(r, j) * lh[r / 3][r % 3];
+                sb += sl.u(r, j) * dh[r / 3][r % 3];
             }
-            a_[k] = sa;
-            b_[k] = sb;
+            av[j] = sa;
+            bv[j] = sb;
         }
-        // dL/dE_e = -(lambda^T g + lambda^T H+ dx) / E
-        double s = 0.0;
-        for (int r = 0; r < 12; ++r) s += lv[r] * ge[r];
-        for (int k = 0; k < 12; ++k) s += a_[k] * fmax(Lm[k], 0.0) * b_[k];
-        dL_dE[e] = -s / Ee;
-        // M = V (F o (a b^T)) V^T, F the divided differences of max(., 0)
-        double Wk[12][12];
-        for (int i = 0; i < 12; ++i)
-            for (int j = 0; j < 12; ++j) {
-                const double li = Lm[i], lj = Lm[j];
-                double f;
-                if (li > 0.0 && lj > 0.0) f = 1.0;
-                else if (li <= 0.0 && lj <= 0.0) f = 0.0;
-                else f = (fmax(li, 0.0) - fmax(lj, 0.0)) / (li - lj);
-                Wk[i][j] = f * a_[i] * b_[j];
-            }
-        double M[12][12];
-        for (int r = 0; r < 12; ++r) {
-            double t[12];
-            for (int j = 0; j < 12; ++j) {
+        // Z = U C U^T with C = (D - 1) o (a b^T), nonzero only where an
+        // eigenvalue is <= 0
+        double Cz[9][9], Zl[9][9];
+#pragma unroll
+        for (int i2 = 0; i2 < 9; ++i2)
+#pragma unroll
+            for (int j = 0; j < 9; ++j) Cz[i2][j] = dd_minus_one(L[i2], L[j]) * av[i2] * bv[j];
+        for (int r = 0; r < 9; ++r) {
+            double tr[9];
+#pragma unroll
+            for (int j = 0; j < 9; ++j) {
                 double acc = 0.0;
-                for (int i = 0; i < 12; ++i) acc += V[r][i] * Wk[i][j];
-                t[j] = acc;
+#pragma unroll
+                for (int i2 = 0; i2 < 9; ++i2) acc += sl.u(r, i2) * Cz[i2][j];
+                tr[j] = acc;
             }
-            for (int c = 0; c < 12; ++c) {
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
                 double acc = 0.0;
-                for (int j = 0; j < 12; ++j) acc += t[j] * V[c][j];
-                M[r][c] = acc;
+#pragma unroll
+                for (int j = 0; j < 9; ++j) acc += tr[j] * sl.u(q, j);
+                Zl[r][q] = acc;
             }
         }
-        // d/dX of lambda^T g(X) + <H(X), M>, one forward-mode pass per coordinate
+        double Xb[4][3] = {};
+        const double psi = reverse_phi(t, mu, lam, lh, false, [&](int r, int q) { return Zl[r][q]; }, Xb);
+        dL_dE[e] -= t.V * psi / Ee;
+#pragma unroll
         for (int a = 0; a < 4; ++a)
-            for (int c = 0; c < 3; ++c) {
-                Dual Xd[4][3];
-                for (int p = 0; p < 4; ++p)
-                    for (int q = 0; q < 3; ++q) Xd[p][q] = {X[p][q], (p == a && q == c) ? 1.0 : 0.0};
-                Dual gd[12], Hd[12][12];
-                stvk_tet<Dual>(Xd, x, mu, lam, gd, Hd);
-                double phi = 0.0;
-                for (int r = 0; r < 12; ++r) {
-                    phi += lv[r] * gd[r].d;
-                    for (int k = 0; k < 12; ++k) phi += M[r][k] * Hd[r][k].d;
-                }
-                atomicAdd(dL_dX + 3 * (int64_t)vid[a] + c, -phi);
-            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) atomicAdd(dL_dX + 3 * (int64_t)vid[a] + c, -Xb[a][c]);
     }
 }
 
@@ -444,43 +967,68 @@ __global__ void restrict_kernel(int32_t n, const int32_t *__restrict__ labels, c
     }
 }
 
+constexpr int64_t kListHeader = 32;  // int32 words before the list (the count, padded to 128 B)
+
+int64_t workspace_words(int64_t n_tets) { return kListHeader + n_tets; }
+
 }  // namespace
+
+extern "C" int64_t agipc_stvk_workspace_bytes(int64_t n_tets)
+{
+    if (n_tets < 0) return -1;
+    return 4 * workspace_words(n_tets);
+}
 
 extern "C" int agipc_fine_assemble_stvk(agipc_ctx *ctx, int32_t n_fine, int64_t n_tets, const int32_t *tets,
                                         const double *X_rest, const double *x, const double *xhat_shift,
                                         const double *E, double nu, const double *mass_h2, const double *g_extra,
                                         const int32_t *fine_row_ptr, const int32_t *fine_col, int64_t fine_nnzb,
-                                        double *fine_val, double *g)
+                                        double *fine_val, double *g, void *workspace, int64_t workspace_bytes)
 {
-    if (!ctx || n_fine <= 0 || n_fine > ctx->max_n || n_tets < 0 || fine_nnzb < n_fine ||
+    if (!ctx || n_fine <= 0 || n_fine > ctx->max_n || n_tets < 0 || n_tets > INT32_MAX || fine_nnzb < n_fine ||
         fine_nnzb > ctx->max_fine_nnzb || !X_rest || !x || !xhat_shift || !mass_h2 || !fine_row_ptr || !fine_col ||
-        !fine_val || !g || (n_tets > 0 && (!tets || !E)) || !(nu > -1.0 && nu < 0.5))
+        !fine_val || !g || (n_tets > 0 && (!tets || !E)) || !(nu > -1.0 && nu < 0.5) || !workspace ||
+        workspace_bytes < 4 * workspace_words(n_tets) || (reinterpret_cast<uintptr_t>(workspace) & 127))
         return AGIPC_ERR_INVALID_ARG;
     cudaStream_t st = ctx->stream;
+    int32_t *ws = static_cast<int32_t *>(workspace);
     Shift3 shift{{xhat_shift[0], xhat_shift[1], xhat_shift[2]}};
     const int tb = 256;
     fine_init_kernel<<<(unsigned)div_up(n_fine, tb), tb, 0, st>>>(n_fine, fine_row_ptr, fine_col, fine_nnzb, mass_h2,
                                                                   x, X_rest, shift, g_extra, fine_val, g, ctx->status);
-    if (n_tets > 0)
-        elem_assemble_kernel<<<(unsigned)min64(div_up(n_tets, 128), (int64_t)ctx->num_sms * 16), 128, 0, st>>>(
-            n_fine, n_tets, tets, fine_row_ptr, fine_col, fine_nnzb, X_rest, x, E, nu, fine_val, g, ctx->status);
+    if (n_tets > 0) {
+        if (cudaMemsetAsync(ws, 0, sizeof(int32_t), st) != cudaSuccess) return AGIPC_ERR_CUDA;
+        elem_pass1_kernel<<<(unsigned)min64(div_up(n_tets, 128), (int64_t)ctx->num_sms * 16), 128, 0, st>>>(
+            n_fine, n_tets, tets, fine_row_ptr, fine_col, fine_nnzb, X_rest, x, E, nu, fine_val, g, ws,
+            ws + kListHeader, ctx->status);
+        elem_pass2_kernel<<<(unsigned)min64(div_up(n_tets, kRefineThreads), (int64_t)ctx->num_sms * 6),
+                            kRefineThreads, 0, st>>>(n_fine, tets, fine_row_ptr, fine_col, fine_nnzb, X_rest, x, E,
+                                                     nu, fine_val, ws, ws + kListHeader, n_tets, ctx->status);
+    }
     return cudaPeekAtLastError() == cudaSuccess ? AGIPC_OK : AGIPC_ERR_CUDA;
 }
 
 extern "C" int agipc_stvk_vjp(agipc_ctx *ctx, int32_t n_fine, int64_t n_tets, const int32_t *tets,
                               const double *X_rest, const double *x, const double *E, double nu,
                               const double *mass_h2, const double *lam, const double *dx, double *dL_dE,
-                              double *dL_dX_rest)
+                              double *dL_dX_rest, void *workspace, int64_t workspace_bytes)
 {
-    if (!ctx || n_fine <= 0 || n_fine > ctx->max_n || n_tets < 0 || !X_rest || !x || !lam || !dx || !dL_dX_rest ||
-        (n_tets > 0 && (!tets || !E || !dL_dE)) || !(nu > -1.0 && nu < 0.5))
+    if (!ctx || n_fine <= 0 || n_fine > ctx->max_n || n_tets < 0 || n_tets > INT32_MAX || !X_rest || !x || !lam ||
+        !dx || !dL_dX_rest || (n_tets > 0 && (!tets || !E || !dL_dE)) || !(nu > -1.0 && nu < 0.5) || !workspace ||
+        workspace_bytes < 4 * workspace_words(n_tets) || (reinterpret_cast<uintptr_t>(workspace) & 127))
         return AGIPC_ERR_INVALID_ARG;
     cudaStream_t st = ctx->stream;
+    int32_t *ws = static_cast<int32_t *>(workspace);
     const int tb = 256;
     vjp_init_kernel<<<(unsigned)div_up(3 * (int64_t)n_fine, tb), tb, 0, st>>>(n_fine, lam, mass_h2, dL_dX_rest);
-    if (n_tets > 0)
-        vjp_kernel<<<(unsigned)min64(div_up(n_tets, 128), (int64_t)ctx->num_sms * 16), 128, 0, st>>>(
-            n_fine, n_tets, tets, X_rest, x, E, nu, lam, dx, dL_dE, dL_dX_rest, ctx->status);
+    if (n_tets > 0) {
+        if (cudaMemsetAsync(ws, 0, sizeof(int32_t), st) != cudaSuccess) return AGIPC_ERR_CUDA;
+        vjp_pass1_kernel<<<(unsigned)min64(div_up(n_tets, 128), (int64_t)ctx->num_sms * 16), 128, 0, st>>>(
+            n_fine, n_tets, tets, X_rest, x, E, nu, lam, dx, dL_dE, dL_dX_rest, ws, ws + kListHeader, ctx->status);
+        vjp_pass2_kernel<<<(unsigned)min64(div_up(n_tets, kRefineThreads), (int64_t)ctx->num_sms * 6),
+                           kRefineThreads, 0, st>>>(n_fine, tets, X_rest, x, E, nu, lam, dx, dL_dE, dL_dX_rest, ws,
+                                                    ws + kListHeader, n_tets);
+    }
     return cudaPeekAtLastError() == cudaSuccess ? AGIPC_OK : AGIPC_ERR_CUDA;
 }
 

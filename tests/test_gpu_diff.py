@@ -140,6 +140,6 @@ def test_bad_tet_index_sets_status():
     E = torch.tensor(pr["E"], dtype=torch.float64, device=dp.x.device)
     X = torch.tensor(pr["X_rest"], dtype=torch.float64, device=dp.x.device)
     agipc.agipc_fine_assemble_stvk(ctx, dp.n, dp.tets, X, dp.x, dp.xhat_shift, E, dp.nu, dp.mass_h2, None,
-                                   dp.row_ptr, dp.col, step.fine_val, step.g)
+                                   dp.row_ptr, dp.col, step.fine_val, step.g, step.workspace)
     assert ctx.status() == agipc.ERR_BAD_INDEX
     ctx.close()
