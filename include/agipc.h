@@ -11,7 +11,8 @@
  *   agipc_prolongate       dx = U^T y                            (Sec. 4.3)
  *
  * plus the precision form (agipc_*_mixed), the differentiation form
- * (agipc_fine_assemble_stvk, agipc_restrict, agipc_stvk_vjp) and
+ * (agipc_fine_assemble_stvk, agipc_restrict, agipc_stvk_vjp), the batched
+ * form (agipc_batch_coarse_offsets, agipc_pcg_batched) and
  * agipc_prolongate_add, agipc_aggregate_static.
  *
  * Conventions for every call:
@@ -133,6 +134,8 @@ typedef struct {
     double tol;          /* stop when ||b - A x||_2 <= tol * ||b||_2 (recurrence residual) */
     int32_t max_iter;    /* iteration cap; reaching it sets AGIPC_ERR_NOT_CONVERGED */
     int32_t rhs_sign;    /* +1 or -1 */
+    int32_t use_x0;      /* agipc_pcg only: nonzero = x holds the initial guess on entry (else x0 = 0);
+                            the stop test stays relative to ||b||; b = 0 gives x = 0 */
 } agipc_pcg_options;
 
 /*
@@ -280,6 +283,54 @@ int agipc_restrict(agipc_ctx *ctx, int32_t n_fine, const int32_t *labels, const 
 int agipc_stvk_vjp(agipc_ctx *ctx, int32_t n_fine, int64_t n_tets, const int32_t *tets, const double *X_rest,
                    const double *x, const double *E, double nu, const double *mass_h2, const double *lam,
                    const double *dx, double *dL_dE, double *dL_dX_rest, void *workspace, int64_t workspace_bytes);
+
+/*
+ * Batched form.  Many independent meshes are concatenated into one
+ * block-diagonal problem: instance i owns fine vertices
+ * [vert_ptr[i], vert_ptr[i+1]) and no edge, tet, stencil or matrix block
+ * couples two instances.  agipc_aggregate, agipc_assemble_coarse_mixed and
+ * agipc_prolongate run on the concatenation unchanged: super-nodes never
+ * cross instances and canonical labels are ranked by the smallest fine
+ * index, so the coarse rows of instance i are the contiguous range
+ * [inst_row[i], inst_row[i+1]) and the coarse matrix is block diagonal too.
+ */
+#define AGIPC_BATCH_MAX_INSTANCES 1024
+
+/*
+ * inst_row[i] = labels[vert_ptr[i]] (the first coarse row of instance i),
+ * inst_row[n_inst] = n_c.
+ *   vert_ptr [n_inst+1] device int32, non-decreasing, vert_ptr[n_inst] = n_fine
+ *   labels [n_fine], n_coarse_dev   from agipc_aggregate
+ *   inst_row [n_inst+1]             out (device)
+ * 1 <= n_inst <= AGIPC_BATCH_MAX_INSTANCES.
+ */
+int agipc_batch_coarse_offsets(agipc_ctx *ctx, int32_t n_inst, int32_t n_fine, const int32_t *vert_ptr,
+                               const int32_t *labels, const int32_t *n_coarse_dev, int32_t *inst_row);
+
+/*
+ * Batched precision-form PCG: solves H_i y_i = sign b_i for every instance i
+ * of a block-diagonal coarse system in one persistent launch, each instance
+ * with its own alpha, beta, stopping test and iteration count, by the method
+ * of agipc_pcg_mixed (FP32 blocks, SpMV and block-Jacobi, FP64 dot products,
+ * FP64 residual replacement every refine_every iterations, true-residual
+ * check before stopping).  Instances that have stopped cost nothing in
+ * later iterations.
+ *   inst_row [n_inst+1]            device, from agipc_batch_coarse_offsets
+ *   max_rows, row_ptr, col, val, val32, dinv32, b, x, opt, refine_every
+ *                                  as agipc_pcg_mixed (the whole concatenation)
+ *   blocks_per_lane                slice width: each warp lane folds this many
+ *                                  consecutive blocks (3, 4, 5 or 6; 0 = 5),
+ *                                  the tile the autotuner picks
+ *   iters_dev [n_inst], relres_dev [n_inst]   out, per instance
+ * A block whose column leaves its instance sets AGIPC_ERR_BAD_INDEX.  Any
+ * instance reaching max_iter sets AGIPC_ERR_NOT_CONVERGED (the others are
+ * still solved).  The per-instance sums use atomics, so results may differ
+ * in the last bits between runs.
+ */
+int agipc_pcg_batched(agipc_ctx *ctx, int32_t n_inst, const int32_t *inst_row, int32_t max_rows,
+                      const int32_t *row_ptr, const int32_t *col, const double *val, const float *val32,
+                      const float *dinv32, const double *b, double *x, const agipc_pcg_options *opt,
+                      int32_t refine_every, int32_t blocks_per_lane, int32_t *iters_dev, double *relres_dev);
 
 /* Bytes of device workspace agipc_fine_assemble_stvk and agipc_stvk_vjp
  * need for n_tets tets (-1 for a negative count). */

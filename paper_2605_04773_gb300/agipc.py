@@ -40,7 +40,8 @@ class AgipcError(RuntimeError):
 
 
 class _PcgOptions(ctypes.Structure):
-    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("rhs_sign", ctypes.c_int32)]
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("rhs_sign", ctypes.c_int32),
+                ("use_x0", ctypes.c_int32)]
 
 
 def library_path() -> str:
@@ -78,12 +79,14 @@ def load():
     lib.agipc_stvk_vjp.argtypes = [P, i32, i64, P, P, P, P, f64, P, P, P, P, P, P, i64]
     lib.agipc_stvk_workspace_bytes.argtypes = [i64]
     lib.agipc_stvk_workspace_bytes.restype = i64
+    lib.agipc_batch_coarse_offsets.argtypes = [P, i32, i32, P, P, P, P]
+    lib.agipc_pcg_batched.argtypes = [P, i32, P, i32, P, P, P, P, P, P, P, ctypes.POINTER(_PcgOptions), i32, i32, P, P]
     lib.agipc_status_string.argtypes = [ctypes.c_int]
     lib.agipc_status_string.restype = ctypes.c_char_p
     for name in ("agipc_create", "agipc_destroy", "agipc_set_stream", "agipc_aggregate", "agipc_assemble_coarse",
                  "agipc_pcg", "agipc_prolongate", "agipc_status", "agipc_aggregate_static",
                  "agipc_assemble_coarse_mixed", "agipc_pcg_mixed", "agipc_prolongate_add", "agipc_fine_assemble_stvk",
-                 "agipc_restrict", "agipc_stvk_vjp"):
+                 "agipc_restrict", "agipc_stvk_vjp", "agipc_batch_coarse_offsets", "agipc_pcg_batched"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -166,8 +169,8 @@ def agipc_assemble_coarse(ctx: Context, n_fine: int, labels, n_coarse_dev, fine_
 
 
 def agipc_pcg(ctx: Context, max_rows: int, n_rows_dev, row_ptr, col, val, dinv, b, x, tol: float, max_iter: int,
-              rhs_sign: int, iters_dev, relres_dev):
-    opt = _PcgOptions(float(tol), int(max_iter), int(rhs_sign))
+              rhs_sign: int, iters_dev, relres_dev, use_x0: bool = False):
+    opt = _PcgOptions(float(tol), int(max_iter), int(rhs_sign), 1 if use_x0 else 0)
     _check(load().agipc_pcg(ctx.handle, int(max_rows), _ptr(n_rows_dev), _ptr(row_ptr), _ptr(col), _ptr(val),
                             _ptr(dinv), _ptr(b), _ptr(x), ctypes.byref(opt), _ptr(iters_dev), _ptr(relres_dev)),
            "agipc_pcg")
@@ -190,7 +193,7 @@ def agipc_assemble_coarse_mixed(ctx: Context, n_fine: int, labels, n_coarse_dev,
 
 def agipc_pcg_mixed(ctx: Context, max_rows: int, n_rows_dev, row_ptr, col, val, val32, dinv32, b, x, tol: float,
                     max_iter: int, rhs_sign: int, refine_every: int, iters_dev, relres_dev):
-    opt = _PcgOptions(float(tol), int(max_iter), int(rhs_sign))
+    opt = _PcgOptions(float(tol), int(max_iter), int(rhs_sign), 0)
     _check(load().agipc_pcg_mixed(ctx.handle, int(max_rows), _ptr(n_rows_dev), _ptr(row_ptr), _ptr(col), _ptr(val),
                                   _ptr(val32), _ptr(dinv32), _ptr(b), _ptr(x), ctypes.byref(opt), int(refine_every),
                                   _ptr(iters_dev), _ptr(relres_dev)), "agipc_pcg_mixed")
@@ -226,6 +229,25 @@ def agipc_stvk_vjp(ctx: Context, n_fine: int, tets, X_rest, x, E, nu: float, mas
     _check(load().agipc_stvk_vjp(ctx.handle, int(n_fine), int(tets.shape[0]), _ptr(tets), _ptr(X_rest), _ptr(x),
                                  _ptr(E), float(nu), _ptr(mass_h2), _ptr(lam), _ptr(dx), _ptr(dL_dE),
                                  _ptr(dL_dX_rest), _ptr(workspace), 8 * int(workspace.numel())), "agipc_stvk_vjp")
+
+
+BATCH_MAX_INSTANCES = 1024
+BATCH_TILES = (3, 4, 5, 6)
+
+
+def agipc_batch_coarse_offsets(ctx: Context, n_inst: int, n_fine: int, vert_ptr, labels, n_coarse_dev, inst_row):
+    _check(load().agipc_batch_coarse_offsets(ctx.handle, int(n_inst), int(n_fine), _ptr(vert_ptr), _ptr(labels),
+                                             _ptr(n_coarse_dev), _ptr(inst_row)), "agipc_batch_coarse_offsets")
+
+
+def agipc_pcg_batched(ctx: Context, n_inst: int, inst_row, max_rows: int, row_ptr, col, val, val32, dinv32, b, x,
+                      tol: float, max_iter: int, rhs_sign: int, refine_every: int, blocks_per_lane: int, iters_dev,
+                      relres_dev):
+    opt = _PcgOptions(float(tol), int(max_iter), int(rhs_sign), 0)
+    _check(load().agipc_pcg_batched(ctx.handle, int(n_inst), _ptr(inst_row), int(max_rows), _ptr(row_ptr), _ptr(col),
+                                    _ptr(val), _ptr(val32), _ptr(dinv32), _ptr(b), _ptr(x), ctypes.byref(opt),
+                                    int(refine_every), int(blocks_per_lane), _ptr(iters_dev), _ptr(relres_dev)),
+           "agipc_pcg_batched")
 
 
 AGGREGATE_STATIC_MAX_NODES = 1 << 20
@@ -371,6 +393,29 @@ class MixedStep(CoarsenedStep):
         return out
 
 
+class PostCoarsening:
+    """Post-coarsening (Sec. 4.3): at most max_iter block-Jacobi PCG
+    iterations on the fine system, started from the prolongated coarse step
+    dx (agipc_pcg with an initial guess).  The fine system is the identity-
+    label assembly (contacts merged, full storage)."""
+
+    def __init__(self, ctx: Context, ds: DeviceScene, tol: float, max_iter: int = 10):
+        self.fine = FineStep(ctx, ds, tol, max_iter)
+        self.ctx, self.ds, self.tol, self.max_iter = ctx, ds, tol, max_iter
+        self.x = torch.empty(ds.n, 3, device=ds.g.device, dtype=torch.float64)
+
+    def assemble(self):
+        self.fine.inner.assemble()
+
+    def refine(self, dx):
+        """x = dx, then up to max_iter PCG iterations on H x = -g."""
+        f = self.fine.inner
+        self.x.copy_(dx)
+        agipc_pcg(self.ctx, self.ds.n, f.n_c, f.row_ptr, f.col, f.val, f.dinv, f.g_c, self.x, self.tol, self.max_iter,
+                  -1, f.iters, f.relres, use_x0=True)
+        return self.x
+
+
 class FineStep:
     """The no-coarsening arm: identity labels (the fine system in full
     storage, contacts merged) and PCG on the fine matrix."""
@@ -510,3 +555,184 @@ class CoarsenedStepFunction(torch.autograd.Function):
 def coarsened_step(E, X_rest, step: DiffStep):
     """Differentiable coarsened Newton step (see CoarsenedStepFunction)."""
     return CoarsenedStepFunction.apply(E, X_rest, step)
+
+
+# ---------------------------------------------------------------------------
+# Batched form
+# ---------------------------------------------------------------------------
+
+
+class BatchDevice:
+    """A Batch's inputs on the device.  Fine blocks and stencils are FP32
+    (the batched form's precision); the gradient is FP64.  Instances whose
+    numpy values are missing (NaN) get them from agipc_fine_assemble_stvk
+    (FP64, then rounded), which evaluates the same StVK physics."""
+
+    def __init__(self, batch, device="cuda"):
+        t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(device=device, dtype=dt)  # noqa: E731
+        self.n = batch.n
+        self.n_inst = batch.n_inst
+        self.vert_ptr = t(batch.vert_ptr, torch.int32)
+        self.edges = t(batch.edges, torch.int32)
+        self.tags = t(batch.tags, torch.uint8)
+        self.row_ptr = t(batch.row_ptr, torch.int32)
+        self.col = t(batch.col, torch.int32)
+        self.pair_idx = t(batch.pair_idx.reshape(-1, 4), torch.int32)
+        self.pair_blk32 = t(batch.pair_blk.reshape(-1, 90), torch.float32)
+        self.pair_idx64 = torch.zeros(0, 4, dtype=torch.int32, device=device)
+        self.pair_blk64 = torch.zeros(0, 90, dtype=torch.float64, device=device)
+        nnzb = int(batch.col.shape[0])
+        missing = batch.val is None or bool(np.isnan(batch.val).any())
+        self.ctx_max_pairs = max(1, int(batch.pair_idx.shape[0]))
+        val = torch.empty(nnzb, 9, dtype=torch.float64, device=device)
+        g = torch.empty(self.n, 3, dtype=torch.float64, device=device)
+        if missing:
+            ctx = Context(self.n, self.edges.shape[0], nnzb, self.ctx_max_pairs)
+            tets = t(batch.tets, torch.int32)
+            ws = stvk_workspace(tets.shape[0], device)
+            shift = tuple(batch.h * batch.h * gv for gv in GRAVITY)
+            agipc_fine_assemble_stvk(ctx, self.n, tets, t(batch.X_rest, torch.float64), t(batch.x, torch.float64),
+                                     shift, t(batch.E, torch.float64), batch.nu, t(batch.mass_h2, torch.float64),
+                                     t(batch.g_pairs, torch.float64), self.row_ptr, self.col, val, g, ws)
+            ctx.check()
+            ctx.close()
+            del tets, ws
+        if batch.val is not None:
+            have = ~np.isnan(batch.val.reshape(nnzb, 9)).any(1)
+            hv = torch.from_numpy(np.ascontiguousarray(batch.val.reshape(nnzb, 9)[have])).to(device)
+            val[torch.from_numpy(np.nonzero(have)[0]).to(device)] = hv
+            gh = ~np.isnan(batch.g).any(1)
+            g[torch.from_numpy(np.nonzero(gh)[0]).to(device)] = torch.from_numpy(
+                np.ascontiguousarray(batch.g[gh])).to(device)
+        self.val32 = val.to(torch.float32)
+        self.g = g
+        del val
+
+    @property
+    def capacity(self) -> int:
+        return 2 * int(self.col.shape[0]) + 16 * int(self.pair_idx.shape[0])
+
+    def context(self) -> Context:
+        return Context(self.n, self.edges.shape[0], self.col.shape[0], self.ctx_max_pairs)
+
+
+class BatchedStep:
+    """The batched coarsened step: labels of the concatenation -> instance
+    offsets -> mixed coarse assembly -> per-instance batched PCG ->
+    prolongation.  run() enqueues it; capture() records it in a CUDA graph
+    that replay() launches as one unit."""
+
+    def __init__(self, ctx: Context, bd: BatchDevice, tol: float, max_iter: int = 100000, refine_every: int = 20,
+                 tile: int = 5):
+        dev = bd.g.device
+        n, cap = bd.n, bd.capacity
+        i32 = dict(device=dev, dtype=torch.int32)
+        f64 = dict(device=dev, dtype=torch.float64)
+        self.ctx, self.bd, self.tol, self.max_iter, self.refine_every, self.tile = ctx, bd, tol, max_iter, \
+            refine_every, tile
+        self.labels = torch.empty(n, **i32)
+        self.n_c = torch.zeros(1, **i32)
+        self.inst_row = torch.zeros(bd.n_inst + 1, **i32)
+        self.row_ptr = torch.empty(n + 1, **i32)
+        self.col = torch.empty(cap, **i32)
+        self.val = torch.empty(cap, 9, **f64)
+        self.val32 = torch.empty(cap, 9, device=dev, dtype=torch.float32)
+        self.nnz = torch.zeros(1, **i32)
+        self.g_c = torch.empty(n, 3, **f64)
+        self.dinv32 = torch.empty(n, 9, device=dev, dtype=torch.float32)
+        self.y = torch.empty(n, 3, **f64)
+        self.dx = torch.empty(n, 3, **f64)
+        self.iters = torch.zeros(bd.n_inst, **i32)
+        self.relres = torch.zeros(bd.n_inst, **f64)
+        self.graph = None
+
+    def run(self):
+        bd, ctx = self.bd, self.ctx
+        agipc_aggregate(ctx, bd.n, bd.edges, bd.tags, self.labels, self.n_c)
+        agipc_batch_coarse_offsets(ctx, bd.n_inst, bd.n, bd.vert_ptr, self.labels, self.n_c, self.inst_row)
+        agipc_assemble_coarse_mixed(ctx, bd.n, self.labels, self.n_c, bd.row_ptr, bd.col, bd.val32, bd.pair_idx,
+                                    bd.pair_blk32, bd.pair_idx64, bd.pair_blk64, bd.g, self.row_ptr, self.col,
+                                    self.val, self.val32, self.nnz, self.g_c, self.dinv32)
+        self.solve()
+        agipc_prolongate(ctx, bd.n, self.labels, self.y, self.dx)
+
+    def solve(self, tile: int = None):
+        agipc_pcg_batched(self.ctx, self.bd.n_inst, self.inst_row, self.bd.n, self.row_ptr, self.col, self.val,
+                          self.val32, self.dinv32, self.g_c, self.y, self.tol, self.max_iter, -1, self.refine_every,
+                          self.tile if tile is None else tile, self.iters, self.relres)
+
+    def capture(self):
+        """Record run() in a CUDA graph on a side stream (the context is
+        switched to that stream for the capture and back afterwards)."""
+        side = torch.cuda.Stream(device=self.bd.g.device)
+        prev = self.ctx.stream
+        side.wait_stream(prev)
+        self.ctx.set_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        try:
+            with torch.cuda.graph(graph, stream=side):
+                self.run()
+        finally:
+            self.ctx.set_stream(prev)
+        prev.wait_stream(side)
+        self.graph = graph
+        return graph
+
+    def replay(self):
+        self.graph.replay()
+
+    def host(self):
+        nc = int(self.n_c.item())
+        nnz = int(self.nnz.item())
+        return dict(labels=self.labels.cpu().numpy(), n_c=nc, inst_row=self.inst_row.cpu().numpy(),
+                    row_ptr=self.row_ptr[:nc + 1].cpu().numpy(), col=self.col[:nnz].cpu().numpy(),
+                    val=self.val[:nnz].cpu().numpy().reshape(-1, 3, 3),
+                    val32=self.val32[:nnz].cpu().numpy().reshape(-1, 3, 3), g_c=self.g_c[:nc].cpu().numpy(),
+                    y=self.y[:nc].cpu().numpy(), dx=self.dx.cpu().numpy(), iters=self.iters.cpu().numpy(),
+                    relres=self.relres.cpu().numpy())
+
+
+def autotune_batched(step: BatchedStep, tiles=BATCH_TILES, reps: int = 3, cache: str = None):
+    """Pick the batched PCG's slice width by timing each candidate on the
+    step's own coarse systems (after one run()), median of reps launches.
+    The choice is cached per device and batch shape in a JSON file (default:
+    next to the library) and set on the step.  Returns (tile, timings_ms)."""
+    import json
+    dev = step.bd.g.device
+    key = "%s|n_inst=%d|n=%d|nnzb=%d" % (torch.cuda.get_device_name(dev), step.bd.n_inst, step.bd.n,
+                                          int(step.bd.col.shape[0]))
+    path = cache or os.path.join(os.path.dirname(library_path()), "autotune_batched.json")
+    table = {}
+    if os.path.exists(path):
+        try:
+            table = json.load(open(path))
+        except (OSError, ValueError):
+            table = {}
+    if key in table and table[key]["tile"] in tiles:
+        step.tile = int(table[key]["tile"])
+        return step.tile, table[key]["ms"]
+    step.run()
+    step.ctx.check()
+    stream = torch.cuda.current_stream(dev)
+    ms = {}
+    for tile in tiles:
+        times = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step.solve(tile)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            times.append(a.elapsed_time(b))
+        step.ctx.check()
+        ms[str(tile)] = float(np.median(times))
+    best = int(min(ms, key=ms.get))
+    step.tile = best
+    table[key] = {"tile": best, "ms": ms}
+    try:
+        with open(path + ".tmp", "w") as f:
+            json.dump(table, f, indent=1)
+        os.replace(path + ".tmp", path)
+    except OSError:
+        pass
+    return best, ms

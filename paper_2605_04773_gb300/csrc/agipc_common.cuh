@@ -35,6 +35,9 @@ struct PcgScratch {
     int max_grid;
 };
 
+constexpr int kBatchMaxInst = 1024;   // instances of one batched PCG launch
+constexpr int kBatchVariants = 4;     // slice widths of the batched PCG (3, 4, 5, 6 blocks per lane)
+
 struct agipc_ctx {
     cudaStream_t stream;
     int device;
@@ -69,6 +72,10 @@ struct agipc_ctx {
     PcgScratch pcg;
     int pcg_block;
     int pcg_grid;
+
+    // batched PCG
+    double *batch_acc;                // [6 * kBatchMaxInst] per-instance sums
+    int batch_grid[kBatchVariants];   // cooperative grid of each slice-width variant
 };
 
 // --------------------------------------------------------------------------

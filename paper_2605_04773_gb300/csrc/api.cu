@@ -11,6 +11,7 @@ int pcg_smem_bytes();
 const void *pcg_kernel_ptr();
 const void *pcg_mixed_kernel_ptr();
 int assemble_long_row_ctas();
+bool batched_configure(agipc_ctx *c);
 
 namespace {
 
@@ -52,6 +53,7 @@ void carve_all(agipc_ctx *c, char *base, size_t *total)
     c->pcg.rowflag = cv.take<uint8_t>(n);
     c->pcg.partials = cv.take<double>(2 * (size_t)c->pcg.max_grid * 4);
     c->pcg.bar = cv.take<unsigned>(64);
+    c->batch_acc = cv.take<double>(6 * (size_t)kBatchMaxInst);
     *total = cv.off;
 }
 
@@ -127,6 +129,10 @@ extern "C" int agipc_create(agipc_ctx **out, void *cuda_stream, int32_t max_fine
     c->pcg_block = pcg_block_size();
     c->pcg_grid = std::min(std::min(per_sm, per_sm_mixed), cap_per_sm) * c->num_sms;
     c->pcg.max_grid = c->pcg_grid;
+    if (!batched_configure(c)) {
+        delete c;
+        return AGIPC_ERR_CUDA;
+    }
 
     size_t bytes = 0;
     carve_all(c, nullptr, &bytes);

@@ -57,6 +57,7 @@ struct PcgArgs {
     double sign;
     double tol;
     int32_t max_iter;
+    int32_t use_x0;
     int32_t max_rows;
     int64_t max_nnzb;
     int32_t *iters_dev;
@@ -101,7 +102,7 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_kernel(PcgArgs A)
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_scal[2];
     __shared__ double s_tot[4];
-    __shared__ double s_grid[3];
+    __shared__ double s_grid[4];
     __shared__ int s_dec;
 
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -144,8 +145,11 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_kernel(PcgArgs A)
     unsigned char *join = wbuf + 2 * kBufBytes;
     double *s_part = reinterpret_cast<double *>(smem + (size_t)kPcgWarps * kWarpSmem);
 
-    // ---- setup: block rows, split flags, x = 0, r = b, u = M^-1 r, p = s = w = 0
-    double gpart = 0.0, rpart = 0.0;
+    // ---- setup: block rows, split flags, x = 0 (or the given x0), r = b - A x0,
+    // u = M^-1 r, p = s = w = 0; with x0 the residual needs A x0, so it is
+    // formed after a first slice pass
+    const bool x0 = A.use_x0 != 0;
+    double gpart = 0.0, rpart = 0.0, bpart = 0.0;
     for (int64_t i = row0 + threadIdx.x; i < row1; i += blockDim.x) {
         const int32_t k0 = A.rp[i], k1 = A.rp[i + 1];
         bool bad = k0 < 0 || k1 < k0 || k1 > nnz;
@@ -162,12 +166,14 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_kernel(PcgArgs A)
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             rr[c] = A.sign * A.b[3 * i + c];
-            x[3 * i + c] = 0.0;
+            bpart += rr[c] * rr[c];
+            if (!x0) x[3 * i + c] = 0.0;
             p[3 * i + c] = 0.0;
             s[3 * i + c] = 0.0;
             w[3 * i + c] = 0.0;
             r[3 * i + c] = rr[c];
         }
+        if (x0) continue;
         const double *D = A.dinv + 9 * i;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -177,15 +183,52 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_kernel(PcgArgs A)
             rpart += rr[c] * rr[c];
         }
     }
+    bool ok = true;
+    if (x0) {
+        if (!grid_sync(count, nblocks, epoch, A.status)) ok = false;
+        if (ok && ld_acquire_u32(A.S.bar + 32) != 0u) {
+            if (gtid == 0) set_status(A.status, ST_BAD_INDEX);
+            ok = false;
+        }
+        // w = A x0, one slice at a time
+        double unused = 0.0;
+        for (int64_t sl = gwarp; ok && sl < nslices; sl += nwarps) {
+            issue_slice(wbuf, sl, nnz, A.val, A.col, brow, lane);
+            cp_async_commit();
+            cp_async_wait<0>();
+            __syncwarp();
+            const int cnt = (int)min64(kSlice, nnz - sl * kSlice);
+            slice_spmv<double, false>(wbuf, cnt, x, w, rowflag, join, lane, unused);
+        }
+        if (ok && !grid_sync(count, nblocks, epoch, A.status)) ok = false;
+        for (int64_t i = row0 + threadIdx.x; ok && i < row1; i += blockDim.x) {
+            double rr[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                rr[c] = fma(A.sign, A.b[3 * i + c], -__ldcg(w + 3 * i + c));
+                r[3 * i + c] = rr[c];
+                w[3 * i + c] = 0.0;
+            }
+            const double *D = A.dinv + 9 * i;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const double uc = D[3 * c] * rr[0] + D[3 * c + 1] * rr[1] + D[3 * c + 2] * rr[2];
+                u[3 * i + c] = uc;
+                gpart += rr[c] * uc;
+                rpart += rr[c] * rr[c];
+            }
+        }
+    }
     {
-        double v[2] = {gpart, rpart};
-        cta_sum<2>(v, s_part, s_tot);
+        double v[3] = {gpart, rpart, bpart};
+        cta_sum<3>(v, s_part, s_tot);
         if (threadIdx.x == 0) {
             partials[blockIdx.x * 4 + 0] = v[0];
             partials[blockIdx.x * 4 + 1] = v[1];
+            partials[blockIdx.x * 4 + 3] = v[2];
         }
     }
-    bool ok = grid_sync(count, nblocks, epoch, A.status);
+    ok = grid_sync(count, nblocks, epoch, A.status) && ok;
     if (ok && ld_acquire_u32(A.S.bar + 32) != 0u) {
         // a row pointer or column index out of range: nothing gathers through it
         if (gtid == 0) set_status(A.status, ST_BAD_INDEX);
@@ -252,8 +295,9 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_kernel(PcgArgs A)
 
         // ---- global scalars: every CTA reduces all slots in the same order;
         // thread 0 alone does the FP64 divisions and square root.
-        if (wib < 3) {
-            // warp k reduces scalar k of all CTAs (fixed order)
+        if (wib < 4) {
+            // warp k reduces scalar k of all CTAs (fixed order); slot 3 holds
+            // ||b||^2 in the first iteration
             double pv[kMaxGridLanes];
 #pragma unroll
             for (int q = 0; q < kMaxGridLanes; ++q) {
@@ -269,7 +313,7 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_kernel(PcgArgs A)
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            const double g = s_grid[0], rh = s_grid[1], dl = s_grid[2];
+            const double g = s_grid[0], rh = s_grid[1], dl = s_grid[2], bb = s_grid[3];
             // 0 iterate, 1 converged, 2 iteration cap, 3 non-finite.  The test
             // ||r|| <= tol ||b|| is done on squares; alpha needs one division:
             // g / (dl - beta g / alpha_old) with beta = g / gamma_old equals
@@ -277,7 +321,7 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_kernel(PcgArgs A)
             int decision = 0;
             double alpha = 0.0, beta = 0.0;
             rnorm2 = rh;
-            if (it == 0) bnorm2 = rh;
+            if (it == 0) bnorm2 = bb;
             if (!isfinite(rh) || !isfinite(g) || !isfinite(dl)) decision = 3;
             else if (bnorm2 == 0.0 || rh <= tol2 * bnorm2) decision = 1;
             else if (it >= A.max_iter) decision = 2;
@@ -349,6 +393,13 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_kernel(PcgArgs A)
         *A.relres_dev = bnorm2 > 0.0 ? sqrt(rnorm2 / bnorm2) : 0.0;
         if (ok && !converged) set_status(A.status, ST_NOT_CONVERGED);
     }
+    // b = 0: the solution is 0 whatever the initial guess
+    if (ok && converged && bnorm2 == 0.0 && x0)
+        for (int64_t i = row0 + threadIdx.x; i < row1; i += blockDim.x) {
+            x[3 * i] = 0.0;
+            x[3 * i + 1] = 0.0;
+            x[3 * i + 2] = 0.0;
+        }
 }
 
 }  // namespace
@@ -381,6 +432,7 @@ extern "C" int agipc_pcg(agipc_ctx *ctx, int32_t max_rows, const int32_t *n_rows
     A.sign = (double)opt->rhs_sign;
     A.tol = opt->tol;
     A.max_iter = opt->max_iter;
+    A.use_x0 = opt->use_x0 != 0;
     A.max_rows = max_rows;
     A.max_nnzb = ctx->max_nnzb;
     A.iters_dev = iters_dev;

@@ -372,7 +372,7 @@ extern "C" int agipc_pcg_mixed(agipc_ctx *ctx, int32_t max_rows, const int32_t *
     if (!ctx || !opt || max_rows < 0 || max_rows > ctx->max_n || !n_rows_dev || !row_ptr || !val || !val32 ||
         !dinv32 || !b || !x || !iters_dev || !relres_dev || refine_every < 0)
         return AGIPC_ERR_INVALID_ARG;
-    if (!(opt->tol >= 0.0) || opt->max_iter < 0 || (opt->rhs_sign != 1 && opt->rhs_sign != -1))
+    if (!(opt->tol >= 0.0) || opt->max_iter < 0 || (opt->rhs_sign != 1 && opt->rhs_sign != -1) || opt->use_x0)
         return AGIPC_ERR_INVALID_ARG;
     if (((uintptr_t)val & 15u) != 0 || ((uintptr_t)val32 & 15u) != 0 || ((uintptr_t)col & 15u) != 0 ||
         ((uintptr_t)dinv32 & 3u) != 0 || ((uintptr_t)b & 7u) != 0 || ((uintptr_t)x & 7u) != 0)

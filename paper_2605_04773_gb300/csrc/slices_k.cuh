@@ -1,0 +1,169 @@
+// Warp slices with a compile-time width and instance-aligned placement, for
+// the batched PCG.  A slice covers up to 32*K consecutive 3x3 blocks; lane L
+// folds blocks L*K .. L*K+K-1 of the slice.  A slice is staged from a block
+// index that is a multiple of 4 (so every cp.async source is 16-byte
+// aligned in FP32 and FP64) and only its positions [qlo, cnt) are valid: the
+// positions before qlo belong to the previous instance and are ignored.
+#pragma once
+
+#include "pcg_slices.cuh"
+
+namespace bsl {
+
+using pcgs::cp_async16;
+using pcgs::dsel;
+using pcgs::store_row;
+
+template <class T, int K>
+struct Geom {
+    static constexpr int kSlice = 32 * K;
+    static constexpr int kValBytes = kSlice * 9 * (int)sizeof(T);
+    static constexpr int kIdxBytes = kSlice * 4;
+    static constexpr int kBufBytes = kValBytes + 2 * kIdxBytes;
+};
+constexpr int kJoinBytes = 32 * (3 * 8 + 3 * 4);
+
+// Stage blocks [abase, abase + cnt) (values, columns, block rows); abase is a
+// multiple of 4.  Bytes past cnt are zero-filled; nothing past the arrays is
+// read.
+template <class T, int K>
+__device__ __forceinline__ void stage(unsigned char *buf, int64_t abase, int cnt, const T *val, const int32_t *col,
+                                      const int32_t *brow, int lane)
+{
+    using G = Geom<T, K>;
+    const int vbytes = 9 * (int)sizeof(T) * cnt, ibytes = 4 * cnt;
+    const unsigned char *vs = reinterpret_cast<const unsigned char *>(val + 9 * abase);
+    const unsigned char *cs = reinterpret_cast<const unsigned char *>(col + abase);
+    const unsigned char *rs = reinterpret_cast<const unsigned char *>(brow + abase);
+    for (int q = lane; 16 * q < vbytes; q += 32) cp_async16(buf + 16 * q, vs + 16 * q, min(16, vbytes - 16 * q));
+    for (int q = lane; 16 * q < ibytes; q += 32) {
+        cp_async16(buf + G::kValBytes + 16 * q, cs + 16 * q, min(16, ibytes - 16 * q));
+        cp_async16(buf + G::kValBytes + G::kIdxBytes + 16 * q, rs + 16 * q, min(16, ibytes - 16 * q));
+    }
+}
+
+// w = A u over the valid positions of one staged slice (rows inside the
+// slice stored, rows cut by its ends added atomically); with kDelta returns
+// this lane's share of u . A u (accumulated in T, per row segment end).
+// Same folding as pcgs::slice_spmv: one running accumulator per lane reset
+// by selects at row starts, 9 FMAs per block, segments that cross lanes
+// joined by the lane where the row starts.
+template <class T, bool kDelta, int K>
+__device__ __forceinline__ double spmv(const unsigned char *buf, int qlo, int cnt, const T *u, T *w,
+                                       const uint8_t *rowflag, unsigned char *join, int lane)
+{
+    using G = Geom<T, K>;
+    const T *s_val = reinterpret_cast<const T *>(buf);
+    const int32_t *s_col = reinterpret_cast<const int32_t *>(buf + G::kValBytes);
+    const int32_t *s_row = reinterpret_cast<const int32_t *>(buf + G::kValBytes + G::kIdxBytes);
+    int rows_[K];
+    T xv[K][3];
+    T ur[K][3];
+    bool split[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const int q = lane * K + j;
+        rows_[j] = -1;
+        split[j] = false;
+        xv[j][0] = xv[j][1] = xv[j][2] = T(0);
+        ur[j][0] = ur[j][1] = ur[j][2] = T(0);
+        if (q >= qlo && q < cnt) {
+            const int rj = s_row[q];
+            rows_[j] = rj;
+            const T *uc = u + 3 * (int64_t)s_col[q];
+            xv[j][0] = __ldcg(uc);
+            xv[j][1] = __ldcg(uc + 1);
+            xv[j][2] = __ldcg(uc + 2);
+            if (j == 0 || q == qlo || rj != s_row[q - 1]) {  // first block of a row segment
+                const T *up = u + 3 * (int64_t)rj;
+                ur[j][0] = __ldcg(up);
+                ur[j][1] = __ldcg(up + 1);
+                ur[j][2] = __ldcg(up + 2);
+                split[j] = (__ldcg(rowflag + rj) & 1) != 0;
+            }
+        }
+    }
+    T acc[3] = {T(0), T(0), T(0)};
+    T fa[3] = {T(0), T(0), T(0)}, la[3] = {T(0), T(0), T(0)};
+    T dloc = T(0);
+    int fr = -1, lr = -1;
+    bool f_split = false, l_split = false, s_cur = false, first_open = true;
+    T cu[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const bool valid = rows_[j] >= 0;
+        const bool start = valid && (j == 0 || rows_[j] != rows_[j - 1]);
+        const bool end = valid && (j == K - 1 || rows_[j + 1] != rows_[j]);
+        // positions outside [qlo, cnt) read stale or foreign shared memory:
+        // select zeros for them
+        const T *Bs = s_val + 9 * (lane * K + j);
+        T B[9];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) B[e] = dsel(valid, Bs[e], T(0));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            cu[c] = dsel(start, ur[j][c], cu[c]);
+            acc[c] = dsel(start, T(0), acc[c]);
+            acc[c] = fma(B[3 * c + 2], xv[j][2], fma(B[3 * c + 1], xv[j][1], fma(B[3 * c], xv[j][0], acc[c])));
+        }
+        s_cur = start ? split[j] : s_cur;
+        if (kDelta)
+            dloc = fma(dsel(end, cu[0], T(0)), acc[0],
+                       fma(dsel(end, cu[1], T(0)), acc[1], fma(dsel(end, cu[2], T(0)), acc[2], dloc)));
+        if (end) {
+            const bool last = j == K - 1 || rows_[j + 1] < 0;
+            if (first_open) {
+                fr = rows_[j];
+                f_split = s_cur;
+                fa[0] = acc[0];
+                fa[1] = acc[1];
+                fa[2] = acc[2];
+                first_open = false;
+            } else if (last) {
+                lr = rows_[j];
+                l_split = s_cur;
+                la[0] = acc[0];
+                la[1] = acc[1];
+                la[2] = acc[2];
+            } else {
+                store_row(w, rows_[j], s_cur, acc);
+            }
+        }
+    }
+    const bool single = lr < 0;
+    T *s_fa = reinterpret_cast<T *>(join);
+    int32_t *s_fr = reinterpret_cast<int32_t *>(join + 32 * 24);
+    int32_t *s_single = s_fr + 32;
+    int32_t *s_last = s_fr + 64;
+    s_fr[lane] = fr;
+    s_single[lane] = single ? 1 : 0;
+    s_last[lane] = single ? fr : lr;
+    s_fa[3 * lane] = fa[0];
+    s_fa[3 * lane + 1] = fa[1];
+    s_fa[3 * lane + 2] = fa[2];
+    __syncwarp();
+    if (!single) {
+        for (int q = lane + 1; q < 32 && s_fr[q] == lr; ++q) {
+            la[0] += s_fa[3 * q];
+            la[1] += s_fa[3 * q + 1];
+            la[2] += s_fa[3 * q + 2];
+            if (!s_single[q]) break;
+        }
+        store_row(w, lr, l_split, la);
+    }
+    if (fr >= 0 && (lane == 0 || s_last[lane - 1] != fr)) {
+        if (single) {
+            for (int q = lane + 1; q < 32 && s_fr[q] == fr; ++q) {
+                fa[0] += s_fa[3 * q];
+                fa[1] += s_fa[3 * q + 1];
+                fa[2] += s_fa[3 * q + 2];
+                if (!s_single[q]) break;
+            }
+        }
+        store_row(w, fr, f_split, fa);
+    }
+    __syncwarp();
+    return (double)dloc;
+}
+
+}  // namespace bsl

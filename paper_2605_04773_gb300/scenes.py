@@ -584,3 +584,164 @@ def diff_problem(sc: Scene) -> dict:
                 row_ptr=sc.row_ptr, col=sc.col, x=m["x"], X_rest=m["X_rest"], E=np.asarray(m["E_elem"]),
                 nu=m["nu"], h=h, mass_h2=m["mass"] / (h * h), pair_idx=sc.pair_idx, pair_blk=sc.pair_blk,
                 g_pairs=m["g_pairs"], x_target=x_target)
+
+
+# ----------------------------------------------------------------------------
+# Batched form: many independent meshes of uneven sizes
+# ----------------------------------------------------------------------------
+
+# Upward edge vectors of the Kuhn split (all cube edges, the monotone face
+# diagonals and the main diagonal), in the order of their index offsets.
+KUHN_UP = ((1, 0, 0), (0, 1, 0), (1, 1, 0), (0, 0, 1), (1, 0, 1), (0, 1, 1), (1, 1, 1))
+
+
+def kuhn_structure(nx: int, ny: int, nz: int):
+    """Edges (u < v, lexicographic) and the upper BSR structure (row_ptr,
+    col: the diagonal then the upward neighbours, sorted) of kuhn_hex_grid's
+    mesh, written down directly: vertex (i, j, k) joins (i, j, k) + v for
+    every v in KUHN_UP that stays in the grid."""
+    ix, iy, iz = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), np.arange(nz + 1), indexing="ij")
+    ix, iy, iz = (a.transpose(2, 1, 0).ravel() for a in (ix, iy, iz))
+    n = ix.size
+    sx, sy = 1, nx + 1
+    sz = (nx + 1) * (ny + 1)
+    v = np.arange(n, dtype=np.int64)
+    cols = [v]
+    valid = [np.ones(n, bool)]
+    for dx, dy, dz in KUHN_UP:
+        cols.append(v + dx * sx + dy * sy + dz * sz)
+        valid.append((ix + dx <= nx) & (iy + dy <= ny) & (iz + dz <= nz))
+    C = np.stack(cols, 1)
+    Vm = np.stack(valid, 1)
+    row_ptr = np.zeros(n + 1, np.int64)
+    np.cumsum(Vm.sum(1), out=row_ptr[1:])
+    col = C[Vm]
+    rows = np.repeat(v, Vm[:, 1:].sum(1))
+    edges = np.stack([rows, C[:, 1:][Vm[:, 1:]]], 1)
+    return edges.astype(np.int32), row_ptr.astype(np.int32), col.astype(np.int32)
+
+
+@dataclasses.dataclass
+class Batch:
+    """Independent instances concatenated into one block-diagonal problem.
+    Instance i owns vertices [vert_ptr[i], vert_ptr[i+1]) and tets
+    [tet_ptr[i], tet_ptr[i+1]); every index array is global."""
+    n_inst: int
+    vert_ptr: np.ndarray
+    tet_ptr: np.ndarray
+    dims: np.ndarray          # [n_inst, 3] cells per axis
+    frac: np.ndarray          # collapsible fraction per instance
+    edges: np.ndarray
+    tags: np.ndarray
+    row_ptr: np.ndarray
+    col: np.ndarray
+    tets: np.ndarray
+    X_rest: np.ndarray
+    x: np.ndarray
+    E: np.ndarray
+    nu: float
+    h: float
+    mass_h2: np.ndarray
+    pair_idx: np.ndarray
+    pair_blk: np.ndarray
+    g_pairs: np.ndarray
+    val: np.ndarray = None    # fine upper blocks (numpy-built batches only)
+    g: np.ndarray = None
+
+    @property
+    def n(self) -> int:
+        return int(self.vert_ptr[-1])
+
+    def instance(self, i: int) -> Scene:
+        """Instance i as a Scene (local indices); needs the numpy values."""
+        v0, v1 = int(self.vert_ptr[i]), int(self.vert_ptr[i + 1])
+        e_sel = (self.edges[:, 0] >= v0) & (self.edges[:, 0] < v1)
+        p_sel = (self.pair_idx[:, 0] >= v0) & (self.pair_idx[:, 0] < v1) if self.pair_idx.size else np.zeros(0, bool)
+        b0, b1 = int(self.row_ptr[v0]), int(self.row_ptr[v1])
+        return Scene(name="batch_%d" % i, seed=-1, n=v1 - v0, edges=self.edges[e_sel] - v0, tags=self.tags[e_sel],
+                     row_ptr=self.row_ptr[v0:v1 + 1] - b0, col=self.col[b0:b1] - v0, val=self.val[b0:b1],
+                     pair_idx=self.pair_idx[p_sel] - v0, pair_blk=self.pair_blk[p_sel], g=self.g[v0:v1],
+                     meta=dict(instance=i))
+
+
+def batch_instances(seed: int = 1004, n_inst: int = 256, v_range=(2000, 60000), frac_range=(0.3, 0.9),
+                    pair_frac_range=(0.0, 0.05), cell: float = 0.01, E: float = 1e5, nu: float = 0.4,
+                    with_values=False) -> Batch:
+    """The batched workload: n_inst hex-grid bodies split into Kuhn tets,
+    vertex counts log-uniform in v_range, random aspect ratios (each axis
+    ratio e^U(-0.7, 0.7)), a collapsible fraction U(frac_range) per instance,
+    U(pair_frac_range) of each instance's vertices in point-triangle barrier
+    stencils (gap U(0.1, 1) dhat), StVK E, nu, rho = 1000, h = 1/60 s.
+    with_values (True, or a collection of instance indices) also sums the
+    fine system in numpy for those instances (val, g; NaN elsewhere): small
+    batches, or the instances a check samples.  The rest get their values on
+    the GPU from the same physics."""
+    rho, h, dhat = 1000.0, 1.0 / 60.0, 1e-3
+    vptr, tptr, dims, fracs = [0], [0], [], []
+    parts = {k: [] for k in ("edges", "tags", "row_ptr", "col", "tets", "X", "x", "mass", "pidx", "pblk", "pgrad",
+                             "val", "g")}
+    nnz_off = 0
+    for i in range(n_inst):
+        rng = np.random.default_rng([seed, i])
+        nv = float(np.exp(rng.uniform(np.log(v_range[0]), np.log(v_range[1]))))
+        rx, ry = np.exp(rng.uniform(-0.7, 0.7, size=2))
+        t = (nv / (rx * ry)) ** (1.0 / 3.0)
+        nx, ny, nz = (max(2, int(round(r * t)) - 1) for r in (rx, ry, 1.0))
+        frac = float(rng.uniform(*frac_range))
+        X, tets = kuhn_hex_grid(nx, ny, nz, cell)
+        edges, row_ptr, col = kuhn_structure(nx, ny, nz)
+        n = X.shape[0]
+        x = X + 0.05 * cell * rng.standard_normal(X.shape)
+        tags = tags_from_field(edges, activity_field(X, rng), frac)
+        vol = np.abs(np.linalg.det(X[tets[:, 1:]] - X[tets[:, :1]])) / 6.0
+        mass = np.bincount(tets.reshape(-1), weights=np.repeat(rho * vol / 4.0, 4), minlength=n)
+        npair = int(rng.uniform(*pair_frac_range) * n) // 4
+        if npair:
+            pidx = np.stack([rng.choice(n, size=4, replace=False) for _ in range(npair)], 0)
+            grad_d = _random_pt_grad(rng, _unit(rng.standard_normal((npair, 3))))
+            d = rng.uniform(0.1, 1.0, size=npair) * dhat
+            pgrad, pblk = barrier_stencils(grad_d, d, dhat, E * cell)
+        else:
+            pidx, pgrad, pblk = np.zeros((0, 4), np.int64), np.zeros((0, 12)), np.zeros((0, 10, 3, 3))
+        g_pairs = _scatter_grad(n, pidx, pgrad.reshape(-1, 4, 3)) if npair else np.zeros((n, 3))
+        off = vptr[-1]
+        parts["edges"].append(edges + off)
+        parts["tags"].append(tags)
+        parts["row_ptr"].append(row_ptr[:-1] + nnz_off)
+        parts["col"].append(col + off)
+        parts["tets"].append(tets + off)
+        parts["X"].append(X)
+        parts["x"].append(x)
+        parts["mass"].append(mass)
+        parts["pidx"].append(pidx + off)
+        parts["pblk"].append(pblk)
+        parts["pgrad"].append(g_pairs)
+        want = with_values is True or (with_values is not False and i in with_values)
+        if not want and with_values is not False:
+            parts["g"].append(np.full((n, 3), np.nan))
+            parts["val"].append(np.full((int(row_ptr[-1]), 3, 3), np.nan))
+        if want:
+            _, e_grad, e_hess = stvk_elements(X[tets], x[tets], E, nu)
+            x_hat = X + h * h * GRAVITY
+            parts["g"].append((mass / (h * h))[:, None] * (x - x_hat) + _scatter_grad(n, tets, e_grad.reshape(-1, 4, 3))
+                              + g_pairs)
+            rp2, col2, val = fine_upper_bsr(n, tets, e_hess, mass / (h * h))
+            assert np.array_equal(rp2, row_ptr) and np.array_equal(col2, col)
+            parts["val"].append(val)
+        nnz_off += int(row_ptr[-1])
+        vptr.append(off + n)
+        tptr.append(tptr[-1] + tets.shape[0])
+        dims.append((nx, ny, nz))
+        fracs.append(frac)
+    cat = lambda k, dt: np.ascontiguousarray(np.concatenate(parts[k], 0).astype(dt))  # noqa: E731
+    row_ptr = np.concatenate(parts["row_ptr"] + [np.array([nnz_off])]).astype(np.int32)
+    n_total = vptr[-1]
+    return Batch(n_inst=n_inst, vert_ptr=np.array(vptr, np.int64), tet_ptr=np.array(tptr, np.int64),
+                 dims=np.array(dims, np.int32), frac=np.array(fracs), edges=cat("edges", np.int32),
+                 tags=cat("tags", np.uint8), row_ptr=row_ptr, col=cat("col", np.int32), tets=cat("tets", np.int32),
+                 X_rest=cat("X", np.float64), x=cat("x", np.float64),
+                 E=np.full(int(tptr[-1]), E), nu=nu, h=h, mass_h2=cat("mass", np.float64) / (h * h),
+                 pair_idx=cat("pidx", np.int32).reshape(-1, 4), pair_blk=cat("pblk", np.float64).reshape(-1, 10, 3, 3),
+                 g_pairs=cat("pgrad", np.float64).reshape(n_total, 3),
+                 val=cat("val", np.float64) if with_values is not False else None,
+                 g=cat("g", np.float64) if with_values is not False else None)

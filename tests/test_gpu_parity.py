@@ -257,3 +257,50 @@ def test_pcg_deterministic():
     assert ctx.status() == agipc.OK
     assert torch.equal(y1, step.y)
     ctx.close()
+
+
+@pytest.mark.parametrize("seed", [1001, 1011])
+def test_post_coarsening_matches_oracle_cg_from_dx(seed):
+    # Sec. 4.3: at most 10 fine PCG iterations started from the prolongated
+    # coarse step.  Both sides start from the oracle's dx (an input here),
+    # run exactly 10 iterations, and must agree; CG never raises the energy.
+    sc = scenes.unit_cube(seed=seed)
+    ref = oracle.coarsened_step(sc, tol=1e-8)
+    rp, ci, val = oracle.fine_system(sc)
+    dinv = oracle.block_jacobi(rp, ci, val)
+    x_or, it_or, rr_or, _ = oracle.pcg(rp, ci, val, dinv, -sc.g, 1e-14, 10, x0=ref["dx"])
+    assert it_or == 10
+    ds = agipc.DeviceScene(sc)
+    ctx = ds.context()
+    post = agipc.PostCoarsening(ctx, ds, tol=1e-14, max_iter=10)
+    post.assemble()
+    x = post.refine(torch.tensor(ref["dx"], dtype=torch.float64, device=ds.g.device))
+    rc = ctx.status()
+    assert rc == agipc.ERR_NOT_CONVERGED  # capped at 10, as asked
+    got = x.cpu().numpy()
+    it = int(post.fine.inner.iters.item())
+    rr = float(post.fine.inner.relres.item())
+    ctx.close()
+    assert it == 10
+    assert np.abs(got - x_or).max() <= 1e-9 * np.abs(x_or).max()
+    assert abs(rr - rr_or) <= 1e-6 * rr_or
+    g = sc.g.reshape(-1)
+
+    def energy(v):
+        return g @ v.reshape(-1) + 0.5 * v.reshape(-1) @ oracle.spmv(rp, ci, val, v).reshape(-1)
+
+    assert energy(got) <= energy(ref["dx"]) + 1e-12 * abs(energy(ref["dx"]))
+
+
+def test_pcg_initial_guess_zero_rhs_returns_zero():
+    sc = scenes.tiny_box(seed=21, nx=2, ny=2, nz=2)
+    sc.g = np.zeros_like(sc.g)
+    ds = agipc.DeviceScene(sc)
+    ctx = ds.context()
+    post = agipc.PostCoarsening(ctx, ds, tol=1e-10, max_iter=10)
+    post.assemble()
+    x = post.refine(torch.ones(sc.n, 3, dtype=torch.float64, device=ds.g.device))
+    assert ctx.status() == 0
+    assert float(x.abs().max()) == 0.0
+    assert int(post.fine.inner.iters.item()) == 0
+    ctx.close()
