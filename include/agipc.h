@@ -332,6 +332,25 @@ int agipc_pcg_batched(agipc_ctx *ctx, int32_t n_inst, const int32_t *inst_row, i
                       const float *dinv32, const double *b, double *x, const agipc_pcg_options *opt,
                       int32_t refine_every, int32_t blocks_per_lane, int32_t *iters_dev, double *relres_dev);
 
+/*
+ * Green-strain-increment tags (Sec. 4.2, Eq. 3), the step before
+ * agipc_aggregate: per tet F = Ds Dm^-1 and G = (F^T F - I)/2 at the previous
+ * and the current iterate; a tet with ||G(x_cur) - G(x_prev)||_F > threshold
+ * protects (tag 0) its 6 edges, every other edge is collapsible (tag 1).
+ * The paper uses threshold 5e-5 (5e-4 for twisting scenes).
+ *   tets [n_tets][4], X_rest, x_prev, x_cur [n_fine][3]
+ *   fine_row_ptr, fine_col, fine_nnzb   the fine upper structure, which is
+ *       the static edge-element adjacency: each row holds its diagonal block
+ *       first, then one block per edge (u, v > u); edge k of the sorted edge
+ *       list is the k-th off-diagonal block
+ *   tags [n_edges] out
+ * A tet edge missing from the structure sets AGIPC_ERR_BAD_INDEX.  The
+ * decision is taken on ||.||_F^2 > threshold^2 in FP64.
+ */
+int agipc_strain_tags(agipc_ctx *ctx, int32_t n_fine, int64_t n_tets, const int32_t *tets, const double *X_rest,
+                      const double *x_prev, const double *x_cur, double threshold, const int32_t *fine_row_ptr,
+                      const int32_t *fine_col, int64_t fine_nnzb, int64_t n_edges, uint8_t *tags);
+
 /* Bytes of device workspace agipc_fine_assemble_stvk and agipc_stvk_vjp
  * need for n_tets tets (-1 for a negative count). */
 int64_t agipc_stvk_workspace_bytes(int64_t n_tets);

@@ -182,3 +182,10 @@ def fine_system(scene):
     """The fine system in full storage (identity labels): the no-coarsening arm."""
     lab = np.arange(scene.n, dtype=np.int32)
     return galerkin(lab, scene.n, scene.row_ptr, scene.col, scene.val, scene.pair_idx, scene.pair_blk)
+
+
+def fine_system_csr_blocks(scene):
+    """The full fine system (contacts merged) as a scipy CSR matrix (3n x 3n)."""
+    import scipy.sparse as sp
+    rp, ci, val = fine_system(scene)
+    return sp.bsr_matrix((val, ci, rp), shape=(3 * scene.n, 3 * scene.n)).tocsr()

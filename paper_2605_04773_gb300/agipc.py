@@ -80,13 +80,14 @@ def load():
     lib.agipc_stvk_workspace_bytes.argtypes = [i64]
     lib.agipc_stvk_workspace_bytes.restype = i64
     lib.agipc_batch_coarse_offsets.argtypes = [P, i32, i32, P, P, P, P]
+    lib.agipc_strain_tags.argtypes = [P, i32, i64, P, P, P, P, f64, P, P, i64, i64, P]
     lib.agipc_pcg_batched.argtypes = [P, i32, P, i32, P, P, P, P, P, P, P, ctypes.POINTER(_PcgOptions), i32, i32, P, P]
     lib.agipc_status_string.argtypes = [ctypes.c_int]
     lib.agipc_status_string.restype = ctypes.c_char_p
     for name in ("agipc_create", "agipc_destroy", "agipc_set_stream", "agipc_aggregate", "agipc_assemble_coarse",
                  "agipc_pcg", "agipc_prolongate", "agipc_status", "agipc_aggregate_static",
                  "agipc_assemble_coarse_mixed", "agipc_pcg_mixed", "agipc_prolongate_add", "agipc_fine_assemble_stvk",
-                 "agipc_restrict", "agipc_stvk_vjp", "agipc_batch_coarse_offsets", "agipc_pcg_batched"):
+                 "agipc_restrict", "agipc_stvk_vjp", "agipc_batch_coarse_offsets", "agipc_pcg_batched", "agipc_strain_tags"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -229,6 +230,13 @@ def agipc_stvk_vjp(ctx: Context, n_fine: int, tets, X_rest, x, E, nu: float, mas
     _check(load().agipc_stvk_vjp(ctx.handle, int(n_fine), int(tets.shape[0]), _ptr(tets), _ptr(X_rest), _ptr(x),
                                  _ptr(E), float(nu), _ptr(mass_h2), _ptr(lam), _ptr(dx), _ptr(dL_dE),
                                  _ptr(dL_dX_rest), _ptr(workspace), 8 * int(workspace.numel())), "agipc_stvk_vjp")
+
+
+def agipc_strain_tags(ctx: Context, n_fine: int, tets, X_rest, x_prev, x_cur, threshold: float, fine_row_ptr,
+                      fine_col, tags):
+    _check(load().agipc_strain_tags(ctx.handle, int(n_fine), int(tets.shape[0]), _ptr(tets), _ptr(X_rest),
+                                    _ptr(x_prev), _ptr(x_cur), float(threshold), _ptr(fine_row_ptr), _ptr(fine_col),
+                                    int(fine_col.shape[0]), int(tags.shape[0]), _ptr(tags)), "agipc_strain_tags")
 
 
 BATCH_MAX_INSTANCES = 1024

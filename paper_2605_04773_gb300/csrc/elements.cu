@@ -68,7 +68,7 @@ constexpr float kPdRel = 1e-4f;      // "clearly positive" eigenvalue threshold 
 constexpr int kSweeps32 = 10;        // FP32 Jacobi sweep cap
 constexpr int kSweeps64 = 4;         // FP64 refinement sweep cap
 constexpr int kRefineThreads = 32;   // one warp per block in the refinement kernels
-constexpr int kRefineSlots = 189;    // FP64 words of shared memory per refinement thread (48,384 B a block)
+constexpr int kRefineSlots = 126;    // FP64 words of shared memory per refinement thread (32,256 B a block)
 
 struct Tet {
     double V;           // volume
@@ -305,10 +305,8 @@ __device__ __forceinline__ int flagged_count(const float A[45])
 }
 
 // Shared-memory slots of one refinement thread: U (81 words, column j at
-// 9j), then A (45 words, packed upper), then room for 12 x 9 words of
-// Q-expanded eigenvectors that may overwrite A once it has been read.  Slot
-// s of thread `lane` lives at sm[s * kRefineThreads + lane] so that a
-// warp's accesses hit 32 banks.
+// 9j), then A (45 words, packed upper).  Slot s of thread `lane` lives at
+// sm[s * kRefineThreads + lane] so that a warp's accesses hit 32 banks.
 struct Slots {
     double *base;
     int lane;
@@ -321,7 +319,9 @@ struct Slots {
 // decomposition, orders the flagged eigenvalues first, re-orthonormalises
 // U in FP64 (modified Gram-Schmidt), forms A = U^T M U and runs FP64
 // Jacobi sweeps over every pair (p, q) with p < m_warp (all pairs when
-// all_pairs), m_warp the warp's largest flagged count.  Returns m_warp.
+// all_pairs), m_warp the warp's largest flagged count (the worklist is
+// ordered by flagged count, so a warp's tets mostly share it).  Returns
+// m_warp.
 __device__ int refine64(const Tet &t, double mu, double lam, const Slots &sl, bool all_pairs)
 {
     float A32[45], U32[9][9];
@@ -377,7 +377,6 @@ __device__ int refine64(const Tet &t, double mu, double lam, const Slots &sl, bo
             scale = fmax(scale, fabs(d));
         }
     }
-    const double thr = 1e-300;
     for (int sweep = 0; sweep < kSweeps64; ++sweep) {
         double off = 0.0;
         for (int p = 0; p < m_warp; ++p)
@@ -385,26 +384,34 @@ __device__ int refine64(const Tet &t, double mu, double lam, const Slots &sl, bo
         if (__all_sync(mask, !(off > 1e-15 * scale))) break;
         for (int p = 0; p < m_warp; ++p)
             for (int q = p + 1; q < 9; ++q) {
-                const double apq = sl.a(p, q);
-                const bool rot = fabs(apq) > thr;
-                const double theta = (sl.a(q, q) - sl.a(p, p)) / (2.0 * (rot ? apq : 1.0));
-                double tt = copysign(1.0, theta) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                tt = rot ? tt : 0.0;
-                const double c = 1.0 / sqrt(tt * tt + 1.0);
+                // The angle only decides how much of a_pq is removed, so it is
+                // taken in FP32; c = 1/sqrt(1 + t^2) and s = t c in FP64 keep
+                // the rotation orthogonal to FP64 precision, and the update
+                // is the exact similarity J^T A J with J = [c s; -s c].
+                const double apq = sl.a(p, q), app = sl.a(p, p), aqq = sl.a(q, q);
+                const float fpq = (float)apq;
+                float tf = 0.f;
+                if (fpq != 0.f) {
+                    const float th = ((float)aqq - (float)app) / (2.f * fpq);
+                    tf = copysignf(1.f, th) / (fabsf(th) + sqrtf(fmaf(th, th, 1.f)));
+                    tf = isfinite(tf) ? tf : 0.f;
+                }
+                const double tt = (double)tf;
+                const double c = rsqrt(fma(tt, tt, 1.0));
                 const double s = tt * c;
-                const double tau = s / (1.0 + c);
-                sl.a(p, p) -= tt * apq;
-                sl.a(q, q) += tt * apq;
-                sl.a(p, q) = rot ? 0.0 : apq;
+                const double cc = c * c, ss = s * s, cs = c * s;
+                sl.a(p, p) = fma(cc, app, fma(-2.0 * cs, apq, ss * aqq));
+                sl.a(q, q) = fma(ss, app, fma(2.0 * cs, apq, cc * aqq));
+                sl.a(p, q) = fma(cc - ss, apq, cs * (app - aqq));
                 for (int k = 0; k < 9; ++k) {
                     if (k != p && k != q) {
                         const double akp = sl.a(k, p), akq = sl.a(k, q);
-                        sl.a(k, p) = akp - s * (akq + tau * akp);
-                        sl.a(k, q) = akq + s * (akp - tau * akq);
+                        sl.a(k, p) = fma(c, akp, -s * akq);
+                        sl.a(k, q) = fma(s, akp, c * akq);
                     }
                     const double ukp = sl.u(k, p), ukq = sl.u(k, q);
-                    sl.u(k, p) = ukp - s * (ukq + tau * ukp);
-                    sl.u(k, q) = ukq + s * (ukp - tau * ukq);
+                    sl.u(k, p) = fma(c, ukp, -s * ukq);
+                    sl.u(k, q) = fma(s, ukp, c * ukq);
                 }
             }
     }
@@ -457,23 +464,49 @@ __device__ __forceinline__ void scatter_block(const int32_t *row_ptr, const int3
         for (int d = 0; d < 3; ++d) atomicAdd(dst + (tr ? 3 * d + c : 3 * c + d), blk(c, d));
 }
 
-// Warp-aggregated append to the flagged-tet list.
-__device__ __forceinline__ void enqueue(int32_t *list_count, int32_t *list, int64_t cap, int32_t e, bool flag,
-                                        uint32_t *status)
+// Worklist of flagged tets, ordered by flagged count so that the warps of
+// pass 2 mostly share it.  Workspace words: hdr[1..9] tets per count,
+// hdr[10..18] scatter cursors, then the list, then one count byte per tet.
+constexpr int kHdr = 32;
+
+// Warp-aggregated count of a tet's flagged count m (0 = not flagged).
+__device__ __forceinline__ void count_flag(int32_t *hdr, int m)
 {
     const unsigned mask = __activemask();
-    const unsigned ballot = __ballot_sync(mask, flag);
-    if (!ballot) return;
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(ballot) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(list_count, __popc(ballot));
-    base = __shfl_sync(mask, base, leader);
-    if (flag) {
-        const int64_t at = base + __popc(ballot & ((1u << lane) - 1u));
-        if (at < cap) list[at] = e;
-        else set_status(status, ST_CAPACITY);
+    const unsigned peers = __match_any_sync(mask, m);
+    if ((int)(threadIdx.x & 31) == __ffs(peers) - 1 && m > 0) atomicAdd(hdr + m, __popc(peers));
+}
+
+// list[offset(m) + k] = e for every flagged tet, offset(m) = sum of the
+// counts below m.
+__global__ void bucket_scatter_kernel(int64_t nt, const uint8_t *__restrict__ mcode, int32_t *hdr, int32_t *list)
+{
+    __shared__ int32_t s_off[10];
+    if (threadIdx.x == 0) {
+        int32_t o = 0;
+        for (int m = 1; m <= 9; ++m) {
+            s_off[m] = o;
+            o += hdr[m];
+        }
     }
+    __syncthreads();
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nt; e += (int64_t)gridDim.x * blockDim.x) {
+        const int m = mcode[e];
+        const unsigned mask = __activemask();
+        const unsigned peers = __match_any_sync(mask, m);
+        const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+        int base = 0;
+        if (lane == leader && m > 0) base = atomicAdd(hdr + 9 + m, __popc(peers));
+        base = __shfl_sync(mask, base, leader);
+        if (m > 0 && m <= 9) list[s_off[m] + base + __popc(peers & ((1u << lane) - 1u))] = (int32_t)e;
+    }
+}
+
+__device__ __forceinline__ int64_t flagged_total(const int32_t *hdr)
+{
+    int64_t t = 0;
+    for (int m = 1; m <= 9; ++m) t += hdr[m];
+    return t;
 }
 
 struct Shift3 {
@@ -514,13 +547,13 @@ __global__ void __launch_bounds__(128) elem_pass1_kernel(int32_t n, int64_t nt, 
                                                          const int32_t *__restrict__ col, int64_t nnzb,
                                                          const double *__restrict__ Xr, const double *__restrict__ xc,
                                                          const double *__restrict__ E, double nu, double *fine_val,
-                                                         double *g, int32_t *list_count, int32_t *list,
+                                                         double *g, int32_t *hdr, uint8_t *mcode,
                                                          uint32_t *status)
 {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nt; e += (int64_t)gridDim.x * blockDim.x) {
         int vid[4];
         double X[4][3], x[4][3];
-        bool flag = false;
+        int flag = 0;
         if (!load_tet(tets, e, n, Xr, xc, vid, X, x)) {
             set_status(status, ST_BAD_INDEX);
         } else {
@@ -575,10 +608,11 @@ __global__ void __launch_bounds__(128) elem_pass1_kernel(int32_t n, int64_t nt, 
                 float A32[45], U32[9][9];
                 reduced_m32(t, mu, lam, A32);
                 jacobi9f(A32, U32);
-                flag = flagged_count(A32) > 0;
+                flag = flagged_count(A32);
             }
         }
-        enqueue(list_count, list, nt, (int32_t)e, flag, status);
+        mcode[e] = (uint8_t)flag;
+        count_flag(hdr, flag);
     }
 }
 
@@ -586,12 +620,12 @@ __global__ void __launch_bounds__(128) elem_pass1_kernel(int32_t n, int64_t nt, 
 __global__ void __launch_bounds__(kRefineThreads) elem_pass2_kernel(
     int32_t n, const int32_t *__restrict__ tets, const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
     int64_t nnzb, const double *__restrict__ Xr, const double *__restrict__ xc, const double *__restrict__ E, double nu,
-    double *fine_val, const int32_t *__restrict__ list_count, const int32_t *__restrict__ list, int64_t cap,
+    double *fine_val, const int32_t *__restrict__ hdr, const int32_t *__restrict__ list, int64_t cap,
     uint32_t *status)
 {
     __shared__ double sm[kRefineSlots * kRefineThreads];
     const Slots sl{sm, (int)threadIdx.x};
-    const int64_t cnt = min64((int64_t)*list_count, cap);
+    const int64_t cnt = min64(flagged_total(hdr), cap);
     for (int64_t i = blockIdx.x * (int64_t)kRefineThreads + threadIdx.x; i < cnt;
          i += (int64_t)gridDim.x * kRefineThreads) {
         const int64_t e = list[i];
@@ -603,31 +637,39 @@ __global__ void __launch_bounds__(kRefineThreads) elem_pass2_kernel(
         Tet t;
         tet_eval(X, x, mu, lam, t);
         const int m_w = refine64(t, mu, lam, sl, false);
-        // negative part of the flagged block, then R_i = Q u_i into the
-        // slots from 81 on (A is dead once d is read; U stays intact)
+        // negative part of the flagged block; R_i = Q u_i (12 words) is
+        // written downwards from the top slot once A has been read: R_i
+        // occupies [114 - 12 i, 126 - 12 i), above every column j < m_w <= 6
+        // of U that is still needed.  Wider warps expand on the fly.
         double d[9];
         for (int i2 = 0; i2 < 9; ++i2) {
             const double aii = i2 < m_w ? sl.a(i2, i2) : 0.0;
             d[i2] = aii < 0.0 ? aii : 0.0;
         }
-        for (int i2 = 0; i2 < m_w; ++i2) {
-            double u[9];
+        const bool stored = m_w <= 6;
+        if (stored) {
+            for (int i2 = 0; i2 < m_w; ++i2) {
+                double u[9];
 #pragma unroll
-            for (int r = 0; r < 9; ++r) u[r] = sl.u(r, i2);
+                for (int r = 0; r < 9; ++r) u[r] = sl.u(r, i2);
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+                for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int c = 0; c < 3; ++c)
-                    sl.raw(81 + 12 * i2 + 3 * a + c) = hq(a, 0) * u[c] + hq(a, 1) * u[3 + c] + hq(a, 2) * u[6 + c];
+                    for (int c = 0; c < 3; ++c)
+                        sl.raw(114 - 12 * i2 + 3 * a + c) = hq(a, 0) * u[c] + hq(a, 1) * u[3 + c] + hq(a, 2) * u[6 + c];
+            }
         }
+        auto rq = [&](int i2, int a, int c) -> double {
+            if (stored) return sl.raw(114 - 12 * i2 + 3 * a + c);
+            return hq(a, 0) * sl.u(c, i2) + hq(a, 1) * sl.u(3 + c, i2) + hq(a, 2) * sl.u(6 + c, i2);
+        };
 #pragma unroll
         for (int q = 0; q < 10; ++q) {
             const int sa = pair_s(q), sb = pair_t(q);
             scatter_block(row_ptr, col, nnzb, fine_val, vid, sa, sb,
                           [&](int c, int dd) {
                               double acc = 0.0;
-                              for (int i2 = 0; i2 < m_w; ++i2)
-                                  acc += d[i2] * sl.raw(81 + 12 * i2 + 3 * sa + c) * sl.raw(81 + 12 * i2 + 3 * sb + dd);
+                              for (int i2 = 0; i2 < m_w; ++i2) acc += d[i2] * rq(i2, sa, c) * rq(i2, sb, dd);
                               return -acc;
                           },
                           status);
@@ -823,12 +865,12 @@ __global__ void __launch_bounds__(128) vjp_pass1_kernel(int32_t n, int64_t nt, c
                                                         const double *__restrict__ E, double nu,
                                                         const double *__restrict__ lam_f, const double *__restrict__ dx,
                                                         double *__restrict__ dL_dE, double *dL_dX,
-                                                        int32_t *list_count, int32_t *list, uint32_t *status)
+                                                        int32_t *hdr, uint8_t *mcode, uint32_t *status)
 {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nt; e += (int64_t)gridDim.x * blockDim.x) {
         int vid[4];
         double X[4][3], x[4][3];
-        bool flag = false;
+        int flag = 0;
         if (!load_tet(tets, e, n, Xr, xc, vid, X, x)) {
             set_status(status, ST_BAD_INDEX);
             dL_dE[e] = 0.0;
@@ -851,9 +893,10 @@ __global__ void __launch_bounds__(128) vjp_pass1_kernel(int32_t n, int64_t nt, c
             float A32[45], U32[9][9];
             reduced_m32(t, mu, lam, A32);
             jacobi9f(A32, U32);
-            flag = flagged_count(A32) > 0;
+            flag = flagged_count(A32);
         }
-        enqueue(list_count, list, nt, (int32_t)e, flag, status);
+        mcode[e] = (uint8_t)flag;
+        count_flag(hdr, flag);
     }
 }
 
@@ -873,12 +916,12 @@ __device__ __forceinline__ double dd_minus_one(double li, double lj)
 __global__ void __launch_bounds__(kRefineThreads) vjp_pass2_kernel(
     int32_t n, const int32_t *__restrict__ tets, const double *__restrict__ Xr, const double *__restrict__ xc,
     const double *__restrict__ E, double nu, const double *__restrict__ lam_f, const double *__restrict__ dx,
-    double *__restrict__ dL_dE, double *dL_dX, const int32_t *__restrict__ list_count,
+    double *__restrict__ dL_dE, double *dL_dX, const int32_t *__restrict__ hdr,
     const int32_t *__restrict__ list, int64_t cap)
 {
     __shared__ double sm[kRefineSlots * kRefineThreads];
     const Slots sl{sm, (int)threadIdx.x};
-    const int64_t cnt = min64((int64_t)*list_count, cap);
+    const int64_t cnt = min64(flagged_total(hdr), cap);
     for (int64_t i = blockIdx.x * (int64_t)kRefineThreads + threadIdx.x; i < cnt;
          i += (int64_t)gridDim.x * kRefineThreads) {
         const int64_t e = list[i];
@@ -967,9 +1010,102 @@ __global__ void restrict_kernel(int32_t n, const int32_t *__restrict__ labels, c
     }
 }
 
-constexpr int64_t kListHeader = 32;  // int32 words before the list (the count, padded to 128 B)
+// Green-strain-increment tagging (Sec. 4.2, Eq. 3): every edge starts
+// collapsible; a tet whose ||G(x_cur) - G(x_prev)||_F exceeds the threshold
+// protects its 6 edges.  Edge k is the k-th off-diagonal block of the fine
+// upper structure (diagonal first in each row, edges sorted), so the index
+// of edge (u, v), u < v, is its block position minus u + 1.
+__global__ void tags_init_kernel(int64_t ne, uint8_t *__restrict__ tags)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < ne; k += (int64_t)gridDim.x * blockDim.x)
+        tags[k] = 1;
+}
 
-int64_t workspace_words(int64_t n_tets) { return kListHeader + n_tets; }
+__device__ __forceinline__ void green(const double W[3][3], const double x[4][3], double G[3][3])
+{
+    double F[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            double v = 0.0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) v += (x[k + 1][i] - x[0][i]) * W[k][j];
+            F[i][j] = v;
+        }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const double v = F[0][i] * F[0][j] + F[1][i] * F[1][j] + F[2][i] * F[2][j];
+            G[i][j] = 0.5 * (i == j ? v - 1.0 : v);
+        }
+}
+
+__global__ void strain_tag_kernel(int32_t n, int64_t nt, const int32_t *__restrict__ tets,
+                                  const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col, int64_t nnzb,
+                                  int64_t n_edges, const double *__restrict__ Xr, const double *__restrict__ xp,
+                                  const double *__restrict__ xc, double thr2, uint8_t *tags, uint32_t *status)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nt; e += (int64_t)gridDim.x * blockDim.x) {
+        int vid[4];
+        double X[4][3], x1[4][3], x0[4][3];
+        if (!load_tet(tets, e, n, Xr, xc, vid, X, x1)) {
+            set_status(status, ST_BAD_INDEX);
+            continue;
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) x0[a][c] = xp[3 * (int64_t)vid[a] + c];
+        // Dm^-1 by cofactors
+        double Dm[3][3], W[3][3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) Dm[c][k] = X[k + 1][c] - X[0][c];
+        const double c00 = Dm[1][1] * Dm[2][2] - Dm[1][2] * Dm[2][1];
+        const double c01 = Dm[1][2] * Dm[2][0] - Dm[1][0] * Dm[2][2];
+        const double c02 = Dm[1][0] * Dm[2][1] - Dm[1][1] * Dm[2][0];
+        const double id = 1.0 / (Dm[0][0] * c00 + Dm[0][1] * c01 + Dm[0][2] * c02);
+        W[0][0] = c00 * id;
+        W[0][1] = (Dm[0][2] * Dm[2][1] - Dm[0][1] * Dm[2][2]) * id;
+        W[0][2] = (Dm[0][1] * Dm[1][2] - Dm[0][2] * Dm[1][1]) * id;
+        W[1][0] = c01 * id;
+        W[1][1] = (Dm[0][0] * Dm[2][2] - Dm[0][2] * Dm[2][0]) * id;
+        W[1][2] = (Dm[0][2] * Dm[1][0] - Dm[0][0] * Dm[1][2]) * id;
+        W[2][0] = c02 * id;
+        W[2][1] = (Dm[0][1] * Dm[2][0] - Dm[0][0] * Dm[2][1]) * id;
+        W[2][2] = (Dm[0][0] * Dm[1][1] - Dm[0][1] * Dm[1][0]) * id;
+        double G1[3][3], G0[3][3];
+        green(W, x1, G1);
+        green(W, x0, G0);
+        double d2 = 0.0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const double d = G1[i][j] - G0[i][j];
+                d2 += d * d;
+            }
+        if (!(d2 > thr2)) continue;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = a + 1; b < 4; ++b) {
+                const int32_t lo = min(vid[a], vid[b]), hi = max(vid[a], vid[b]);
+                const int64_t pos = lo == hi ? -1 : find_block(row_ptr, col, nnzb, lo, hi);
+                const int64_t k = pos - (int64_t)lo - 1;
+                if (pos < 0 || k < 0 || k >= n_edges) {
+                    set_status(status, ST_BAD_INDEX);
+                    continue;
+                }
+                tags[k] = 0;
+            }
+    }
+}
+
+int64_t workspace_words(int64_t n_tets) { return kHdr + n_tets + div_up(n_tets, 4); }
 
 }  // namespace
 
@@ -997,13 +1133,17 @@ extern "C" int agipc_fine_assemble_stvk(agipc_ctx *ctx, int32_t n_fine, int64_t 
     fine_init_kernel<<<(unsigned)div_up(n_fine, tb), tb, 0, st>>>(n_fine, fine_row_ptr, fine_col, fine_nnzb, mass_h2,
                                                                   x, X_rest, shift, g_extra, fine_val, g, ctx->status);
     if (n_tets > 0) {
-        if (cudaMemsetAsync(ws, 0, sizeof(int32_t), st) != cudaSuccess) return AGIPC_ERR_CUDA;
+        int32_t *list = ws + kHdr;
+        uint8_t *mcode = reinterpret_cast<uint8_t *>(list + n_tets);
+        if (cudaMemsetAsync(ws, 0, kHdr * sizeof(int32_t), st) != cudaSuccess) return AGIPC_ERR_CUDA;
         elem_pass1_kernel<<<(unsigned)min64(div_up(n_tets, 128), (int64_t)ctx->num_sms * 16), 128, 0, st>>>(
-            n_fine, n_tets, tets, fine_row_ptr, fine_col, fine_nnzb, X_rest, x, E, nu, fine_val, g, ws,
-            ws + kListHeader, ctx->status);
-        elem_pass2_kernel<<<(unsigned)min64(div_up(n_tets, kRefineThreads), (int64_t)ctx->num_sms * 6),
+            n_fine, n_tets, tets, fine_row_ptr, fine_col, fine_nnzb, X_rest, x, E, nu, fine_val, g, ws, mcode,
+            ctx->status);
+        bucket_scatter_kernel<<<(unsigned)min64(div_up(n_tets, 256), (int64_t)ctx->num_sms * 8), 256, 0, st>>>(
+            n_tets, mcode, ws, list);
+        elem_pass2_kernel<<<(unsigned)min64(div_up(n_tets, kRefineThreads), (int64_t)ctx->num_sms * 7),
                             kRefineThreads, 0, st>>>(n_fine, tets, fine_row_ptr, fine_col, fine_nnzb, X_rest, x, E,
-                                                     nu, fine_val, ws, ws + kListHeader, n_tets, ctx->status);
+                                                     nu, fine_val, ws, list, n_tets, ctx->status);
     }
     return cudaPeekAtLastError() == cudaSuccess ? AGIPC_OK : AGIPC_ERR_CUDA;
 }
@@ -1022,12 +1162,16 @@ extern "C" int agipc_stvk_vjp(agipc_ctx *ctx, int32_t n_fine, int64_t n_tets, co
     const int tb = 256;
     vjp_init_kernel<<<(unsigned)div_up(3 * (int64_t)n_fine, tb), tb, 0, st>>>(n_fine, lam, mass_h2, dL_dX_rest);
     if (n_tets > 0) {
-        if (cudaMemsetAsync(ws, 0, sizeof(int32_t), st) != cudaSuccess) return AGIPC_ERR_CUDA;
+        int32_t *list = ws + kHdr;
+        uint8_t *mcode = reinterpret_cast<uint8_t *>(list + n_tets);
+        if (cudaMemsetAsync(ws, 0, kHdr * sizeof(int32_t), st) != cudaSuccess) return AGIPC_ERR_CUDA;
         vjp_pass1_kernel<<<(unsigned)min64(div_up(n_tets, 128), (int64_t)ctx->num_sms * 16), 128, 0, st>>>(
-            n_fine, n_tets, tets, X_rest, x, E, nu, lam, dx, dL_dE, dL_dX_rest, ws, ws + kListHeader, ctx->status);
-        vjp_pass2_kernel<<<(unsigned)min64(div_up(n_tets, kRefineThreads), (int64_t)ctx->num_sms * 6),
+            n_fine, n_tets, tets, X_rest, x, E, nu, lam, dx, dL_dE, dL_dX_rest, ws, mcode, ctx->status);
+        bucket_scatter_kernel<<<(unsigned)min64(div_up(n_tets, 256), (int64_t)ctx->num_sms * 8), 256, 0, st>>>(
+            n_tets, mcode, ws, list);
+        vjp_pass2_kernel<<<(unsigned)min64(div_up(n_tets, kRefineThreads), (int64_t)ctx->num_sms * 7),
                            kRefineThreads, 0, st>>>(n_fine, tets, X_rest, x, E, nu, lam, dx, dL_dE, dL_dX_rest, ws,
-                                                    ws + kListHeader, n_tets);
+                                                    list, n_tets);
     }
     return cudaPeekAtLastError() == cudaSuccess ? AGIPC_OK : AGIPC_ERR_CUDA;
 }
@@ -1044,5 +1188,26 @@ extern "C" int agipc_restrict(agipc_ctx *ctx, int32_t n_fine, const int32_t *lab
     const int tb = 256;
     restrict_kernel<<<(unsigned)min64(div_up(n_fine, tb), (int64_t)ctx->num_sms * 32), tb, 0, st>>>(
         n_fine, labels, n_coarse_dev, v, v_c, ctx->status);
+    return cudaPeekAtLastError() == cudaSuccess ? AGIPC_OK : AGIPC_ERR_CUDA;
+}
+
+extern "C" int agipc_strain_tags(agipc_ctx *ctx, int32_t n_fine, int64_t n_tets, const int32_t *tets,
+                                 const double *X_rest, const double *x_prev, const double *x_cur, double threshold,
+                                 const int32_t *fine_row_ptr, const int32_t *fine_col, int64_t fine_nnzb,
+                                 int64_t n_edges, uint8_t *tags)
+{
+    if (!ctx || n_fine <= 0 || n_fine > ctx->max_n || n_tets < 0 || n_edges < 0 || fine_nnzb < n_fine ||
+        !X_rest || !x_prev || !x_cur || !fine_row_ptr || !fine_col || (n_edges > 0 && !tags) ||
+        (n_tets > 0 && !tets) || !(threshold >= 0.0))
+        return AGIPC_ERR_INVALID_ARG;
+    cudaStream_t st = ctx->stream;
+    const int tb = 256;
+    if (n_edges > 0)
+        tags_init_kernel<<<(unsigned)min64(div_up(n_edges, tb), (int64_t)ctx->num_sms * 32), tb, 0, st>>>(n_edges,
+                                                                                                     tags);
+    if (n_tets > 0)
+        strain_tag_kernel<<<(unsigned)min64(div_up(n_tets, tb), (int64_t)ctx->num_sms * 32), tb, 0, st>>>(
+            n_fine, n_tets, tets, fine_row_ptr, fine_col, fine_nnzb, n_edges, X_rest, x_prev, x_cur,
+            threshold * threshold, tags, ctx->status);
     return cudaPeekAtLastError() == cudaSuccess ? AGIPC_OK : AGIPC_ERR_CUDA;
 }

@@ -304,3 +304,29 @@ def test_pcg_initial_guess_zero_rhs_returns_zero():
     assert float(x.abs().max()) == 0.0
     assert int(post.fine.inner.iters.item()) == 0
     ctx.close()
+
+
+@pytest.mark.parametrize("amp", [0.0, 8e-6, 2e-3])
+def test_strain_tags_match_oracle(amp):
+    # Sec. 4.2, Eq. 3: tags from the Green-strain increment between two
+    # iterates; bit-exact against the oracle (FP64 decision on both sides)
+    from oracle import tagging
+    sc = scenes.unit_cube(seed=1001)
+    X, x, tets = sc.meta["X_rest"], sc.meta["x"], sc.meta["tets"]
+    rng = np.random.default_rng(11)
+    # a smooth random displacement plus a localized bump
+    x1 = x + amp * np.sin(3.0 * X @ rng.standard_normal((3, 3)))
+    x1[rng.choice(sc.n, 5, replace=False)] += 0.01
+    ref, _ = tagging.strain_tags(X, x, x1, tets, sc.edges, 5e-5)
+    t = lambda a, dt: torch.tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")  # noqa: E731
+    ds = agipc.DeviceScene(sc)
+    ctx = ds.context()
+    tags = torch.empty(sc.n_edges, dtype=torch.uint8, device="cuda")
+    agipc.agipc_strain_tags(ctx, sc.n, t(tets, torch.int32), t(X, torch.float64), t(x, torch.float64),
+                            t(x1, torch.float64), 5e-5, ds.row_ptr, ds.col, tags)
+    assert ctx.status() == 0
+    ctx.close()
+    got = tags.cpu().numpy()
+    assert np.array_equal(got, ref)
+    if amp == 8e-6:  # a mix of protected and collapsible edges
+        assert 0 < (ref == 0).sum() < ref.size
