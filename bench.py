@@ -429,8 +429,8 @@ def differentiation_form(dev, steps: int):
         rec["backward"].append(ev[3].elapsed_time(ev[5]))
     ctx.check()
     med = {k: float(np.median(v_)) for k, v_ in rec.items()}
-    ws = step.workspace
-    n_flag = int(ws[0].item() & 0xFFFFFFFF)
+    # workspace header: tets per flagged-eigenvalue count in int32 words 1..9
+    n_flag = int(step.workspace.view(torch.int32)[1:10].sum().item())
     out = {"value": 1e3 / (med["forward"] + med["backward"]), "unit": "gradient evaluations/s",
            "ms_forward": med["forward"], "ms_backward": med["backward"],
            "ms": {k: med[k] for k in names}, "pcg_iters": int(step.iters.item()),

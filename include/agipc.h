@@ -294,7 +294,7 @@ int agipc_stvk_vjp(agipc_ctx *ctx, int32_t n_fine, int64_t n_tets, const int32_t
  * index, so the coarse rows of instance i are the contiguous range
  * [inst_row[i], inst_row[i+1]) and the coarse matrix is block diagonal too.
  */
-#define AGIPC_BATCH_MAX_INSTANCES 1024
+#define AGIPC_BATCH_MAX_INSTANCES 512
 
 /*
  * inst_row[i] = labels[vert_ptr[i]] (the first coarse row of instance i),
@@ -319,7 +319,7 @@ int agipc_batch_coarse_offsets(agipc_ctx *ctx, int32_t n_inst, int32_t n_fine, c
  *   max_rows, row_ptr, col, val, val32, dinv32, b, x, opt, refine_every
  *                                  as agipc_pcg_mixed (the whole concatenation)
  *   blocks_per_lane                slice width: each warp lane folds this many
- *                                  consecutive blocks (3, 4, 5 or 6; 0 = 5),
+ *                                  consecutive blocks (4, 5, 6 or 8; 0 = 5),
  *                                  the tile the autotuner picks
  *   iters_dev [n_inst], relres_dev [n_inst]   out, per instance
  * A block whose column leaves its instance sets AGIPC_ERR_BAD_INDEX.  Any
@@ -350,6 +350,43 @@ int agipc_pcg_batched(agipc_ctx *ctx, int32_t n_inst, const int32_t *inst_row, i
 int agipc_strain_tags(agipc_ctx *ctx, int32_t n_fine, int64_t n_tets, const int32_t *tets, const double *X_rest,
                       const double *x_prev, const double *x_cur, double threshold, const int32_t *fine_row_ptr,
                       const int32_t *fine_col, int64_t fine_nnzb, int64_t n_edges, uint8_t *tags);
+
+/*
+ * Adaptive affine embedding (Sec. 4.2, Eq. 4; the supplement's affine
+ * mapping).  A coarse node whose aggregate holds more than `threshold` fine
+ * nodes (the paper uses 32) gets 12 DoF: fine node f of it moves by
+ * dx_f = A_f^T y_c, A_f = Xbar_f (x) I3, Xbar_f = (X_rest_f, 1), so y_c is four
+ * 3-vectors; smaller aggregates keep dx_f = y_c.  Coarse 3-rows: every 3-DoF
+ * node first, then every 12-DoF node as 4 consecutive rows, each class in
+ * label order.  The coarse system is the Galerkin product with that
+ * prolongation (g_c = P^T g, H_c = P^T H P), stored as a full 3x3 BSR matrix
+ * solvable by agipc_pcg; its block-Jacobi inverses are of the 3x3 diagonal
+ * blocks.
+ *
+ * agipc_affine_plan: coarse_base [n_fine] and coarse_k [n_fine] (first 3-row
+ *   and width, 1 or 4, of every coarse node c < n_c), n_rows_dev (number of
+ *   coarse 3-rows).  threshold >= 3 (then n_rows <= n_fine).
+ * agipc_assemble_affine: label_row_ptr, label_col are the label-level full
+ *   coarse structure (from agipc_assemble_coarse on the same labels); the
+ *   fine upper BSR, stencils and g as agipc_assemble_coarse.  Outputs:
+ *   row_ptr [n_fine+1] (rows past n_rows are empty), col, val [cap][9],
+ *   nnzb_dev, g_c [n_fine][3], dinv [n_fine][9].  Sums use FP64 atomics.
+ * agipc_prolongate_affine: dx = P y.
+ * Labels out of range or blocks missing from the structure set
+ * AGIPC_ERR_BAD_INDEX; overflowing cap_nnzb sets AGIPC_ERR_CAPACITY.
+ */
+int agipc_affine_plan(agipc_ctx *ctx, int32_t n_fine, const int32_t *labels, const int32_t *n_coarse_dev,
+                      int32_t threshold, int32_t *coarse_base, int32_t *coarse_k, int32_t *n_rows_dev);
+int agipc_assemble_affine(agipc_ctx *ctx, int32_t n_fine, const int32_t *labels, const int32_t *n_coarse_dev,
+                          const double *X_rest, const int32_t *coarse_base, const int32_t *coarse_k,
+                          const int32_t *n_rows_dev, const int32_t *label_row_ptr, const int32_t *label_col,
+                          const int32_t *fine_row_ptr, const int32_t *fine_col, const double *fine_val,
+                          int64_t fine_nnzb, int64_t n_pairs, const int32_t *pair_idx, const double *pair_blk,
+                          const double *g, int32_t *row_ptr, int32_t *col, double *val, int64_t cap_nnzb,
+                          int32_t *nnzb_dev, double *g_c, double *dinv);
+int agipc_prolongate_affine(agipc_ctx *ctx, int32_t n_fine, const int32_t *labels, const int32_t *n_coarse_dev,
+                            const double *X_rest, const int32_t *coarse_base, const int32_t *coarse_k,
+                            const double *y, double *dx);
 
 /* Bytes of device workspace agipc_fine_assemble_stvk and agipc_stvk_vjp
  * need for n_tets tets (-1 for a negative count). */

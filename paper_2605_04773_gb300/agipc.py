@@ -81,13 +81,18 @@ def load():
     lib.agipc_stvk_workspace_bytes.restype = i64
     lib.agipc_batch_coarse_offsets.argtypes = [P, i32, i32, P, P, P, P]
     lib.agipc_strain_tags.argtypes = [P, i32, i64, P, P, P, P, f64, P, P, i64, i64, P]
+    lib.agipc_affine_plan.argtypes = [P, i32, P, P, i32, P, P, P]
+    lib.agipc_assemble_affine.argtypes = [P, i32, P, P, P, P, P, P, P, P, P, P, P, i64, i64, P, P, P, P, P, P, i64,
+                                          P, P, P]
+    lib.agipc_prolongate_affine.argtypes = [P, i32, P, P, P, P, P, P, P]
     lib.agipc_pcg_batched.argtypes = [P, i32, P, i32, P, P, P, P, P, P, P, ctypes.POINTER(_PcgOptions), i32, i32, P, P]
     lib.agipc_status_string.argtypes = [ctypes.c_int]
     lib.agipc_status_string.restype = ctypes.c_char_p
     for name in ("agipc_create", "agipc_destroy", "agipc_set_stream", "agipc_aggregate", "agipc_assemble_coarse",
                  "agipc_pcg", "agipc_prolongate", "agipc_status", "agipc_aggregate_static",
                  "agipc_assemble_coarse_mixed", "agipc_pcg_mixed", "agipc_prolongate_add", "agipc_fine_assemble_stvk",
-                 "agipc_restrict", "agipc_stvk_vjp", "agipc_batch_coarse_offsets", "agipc_pcg_batched", "agipc_strain_tags"):
+                 "agipc_restrict", "agipc_stvk_vjp", "agipc_batch_coarse_offsets", "agipc_pcg_batched", "agipc_strain_tags", "agipc_affine_plan", "agipc_assemble_affine",
+                 "agipc_prolongate_affine"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -239,8 +244,8 @@ def agipc_strain_tags(ctx: Context, n_fine: int, tets, X_rest, x_prev, x_cur, th
                                     int(fine_col.shape[0]), int(tags.shape[0]), _ptr(tags)), "agipc_strain_tags")
 
 
-BATCH_MAX_INSTANCES = 1024
-BATCH_TILES = (3, 4, 5, 6)
+BATCH_MAX_INSTANCES = 512
+BATCH_TILES = (4, 5, 6, 8)
 
 
 def agipc_batch_coarse_offsets(ctx: Context, n_inst: int, n_fine: int, vert_ptr, labels, n_coarse_dev, inst_row):
@@ -744,3 +749,82 @@ def autotune_batched(step: BatchedStep, tiles=BATCH_TILES, reps: int = 3, cache:
     except OSError:
         pass
     return best, ms
+
+
+# ---------------------------------------------------------------------------
+# Affine embedding
+# ---------------------------------------------------------------------------
+
+
+def agipc_affine_plan(ctx: Context, n_fine: int, labels, n_coarse_dev, threshold: int, coarse_base, coarse_k,
+                      n_rows_dev):
+    _check(load().agipc_affine_plan(ctx.handle, int(n_fine), _ptr(labels), _ptr(n_coarse_dev), int(threshold),
+                                    _ptr(coarse_base), _ptr(coarse_k), _ptr(n_rows_dev)), "agipc_affine_plan")
+
+
+def agipc_assemble_affine(ctx: Context, n_fine: int, labels, n_coarse_dev, X_rest, coarse_base, coarse_k, n_rows_dev,
+                          label_row_ptr, label_col, fine_row_ptr, fine_col, fine_val, pair_idx, pair_blk, g, row_ptr,
+                          col, val, nnzb_dev, g_c, dinv):
+    _check(load().agipc_assemble_affine(
+        ctx.handle, int(n_fine), _ptr(labels), _ptr(n_coarse_dev), _ptr(X_rest), _ptr(coarse_base), _ptr(coarse_k),
+        _ptr(n_rows_dev), _ptr(label_row_ptr), _ptr(label_col), _ptr(fine_row_ptr), _ptr(fine_col), _ptr(fine_val),
+        int(fine_col.shape[0]), int(pair_idx.shape[0]), _ptr(pair_idx), _ptr(pair_blk), _ptr(g), _ptr(row_ptr),
+        _ptr(col), _ptr(val), int(col.shape[0]), _ptr(nnzb_dev), _ptr(g_c), _ptr(dinv)), "agipc_assemble_affine")
+
+
+def agipc_prolongate_affine(ctx: Context, n_fine: int, labels, n_coarse_dev, X_rest, coarse_base, coarse_k, y, dx):
+    _check(load().agipc_prolongate_affine(ctx.handle, int(n_fine), _ptr(labels), _ptr(n_coarse_dev), _ptr(X_rest),
+                                          _ptr(coarse_base), _ptr(coarse_k), _ptr(y), _ptr(dx)),
+           "agipc_prolongate_affine")
+
+
+class AffineStep(CoarsenedStep):
+    """The coarsened step with affine embedding of aggregates larger than
+    `threshold` fine nodes: labels -> label-level assembly (structure) ->
+    plan -> expanded Galerkin assembly -> PCG -> dx = P y."""
+
+    def __init__(self, ctx: Context, ds: DeviceScene, X_rest, tol: float, threshold: int = 32,
+                 max_iter: int = 100000):
+        super().__init__(ctx, ds, tol, max_iter)
+        dev = ds.g.device
+        n = ds.n
+        self.threshold = threshold
+        self.X_rest = torch.as_tensor(np.ascontiguousarray(X_rest), dtype=torch.float64, device=dev)
+        self.coarse_base = torch.zeros(n, dtype=torch.int32, device=dev)
+        self.coarse_k = torch.zeros(n, dtype=torch.int32, device=dev)
+        self.n_rows = torch.zeros(1, dtype=torch.int32, device=dev)
+        cap = 16 * ds.capacity
+        self.a_row_ptr = torch.empty(n + 1, dtype=torch.int32, device=dev)
+        self.a_col = torch.empty(cap, dtype=torch.int32, device=dev)
+        self.a_val = torch.empty(cap, 9, dtype=torch.float64, device=dev)
+        self.a_nnz = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.a_gc = torch.empty(n, 3, dtype=torch.float64, device=dev)
+        self.a_dinv = torch.empty(n, 9, dtype=torch.float64, device=dev)
+
+    def assemble(self):
+        super().assemble()
+        ds, ctx = self.ds, self.ctx
+        agipc_affine_plan(ctx, ds.n, self.labels, self.n_c, self.threshold, self.coarse_base, self.coarse_k,
+                          self.n_rows)
+        agipc_assemble_affine(ctx, ds.n, self.labels, self.n_c, self.X_rest, self.coarse_base, self.coarse_k,
+                              self.n_rows, self.row_ptr, self.col, ds.row_ptr, ds.col, ds.val, ds.pair_idx,
+                              ds.pair_blk, ds.g, self.a_row_ptr, self.a_col, self.a_val, self.a_nnz, self.a_gc,
+                              self.a_dinv)
+
+    def solve(self):
+        agipc_pcg(self.ctx, self.ds.n, self.n_rows, self.a_row_ptr, self.a_col, self.a_val, self.a_dinv, self.a_gc,
+                  self.y, self.tol, self.max_iter, -1, self.iters, self.relres)
+
+    def prolongate(self):
+        agipc_prolongate_affine(self.ctx, self.ds.n, self.labels, self.n_c, self.X_rest, self.coarse_base,
+                                self.coarse_k, self.y, self.dx)
+
+    def host(self):
+        nr = int(self.n_rows.item())
+        nnz = int(self.a_nnz.item())
+        out = super().host()
+        out.update(n_rows=nr, a_row_ptr=self.a_row_ptr[:nr + 1].cpu().numpy(), a_col=self.a_col[:nnz].cpu().numpy(),
+                   a_val=self.a_val[:nnz].cpu().numpy().reshape(-1, 3, 3), a_gc=self.a_gc[:nr].cpu().numpy(),
+                   y=self.y[:nr].cpu().numpy(), coarse_base=self.coarse_base[:out["n_c"]].cpu().numpy(),
+                   coarse_k=self.coarse_k[:out["n_c"]].cpu().numpy())
+        return out

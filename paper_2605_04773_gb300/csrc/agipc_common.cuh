@@ -35,8 +35,8 @@ struct PcgScratch {
     int max_grid;
 };
 
-constexpr int kBatchMaxInst = 1024;   // instances of one batched PCG launch
-constexpr int kBatchVariants = 4;     // slice widths of the batched PCG (3, 4, 5, 6 blocks per lane)
+constexpr int kBatchMaxInst = 512;    // instances of one batched PCG launch
+constexpr int kBatchVariants = 4;     // slice widths of the batched PCG (4, 5, 6, 8 blocks per lane)
 
 struct agipc_ctx {
     cudaStream_t stream;

@@ -22,7 +22,7 @@
 //             rho are reduced per warp and per CTA before one atomic per
 //             instance and CTA.
 // Instances that have stopped cost nothing in later iterations.  The number
-// of blocks a lane folds (K = 3..6, the slice width 32 K) is a template
+// of blocks a lane folds (K = 4, 5, 6 or 8, the slice width 32 K) is a template
 // parameter chosen by the caller (the Python autotuner picks it by timing).
 // The per-instance sums are added with atomics, so alpha and beta may differ
 // in the last bits from run to run.
@@ -68,7 +68,7 @@ struct Layout {
     static constexpr int kWarps = kPcgWarps * kWarp;
     static constexpr int kInt = 3 * (kBatchMaxInst + 1) * 4 + 4;           // irow, b0, sptr (+pad to 8)
     static constexpr int kDbl = 2 * kBatchMaxInst * 8 + kLocalTab * 2 * 8;  // alpha, beta, local table
-    static constexpr int kScan = (kBatchMaxInst + 1) * 4 * 2;               // active and refine slice prefixes
+    static constexpr int kScan = (kBatchMaxInst + 1) * 4 * 4;               // active/refine slice and row prefixes
     static constexpr int kByte = 2 * kBatchMaxInst;                         // dec, ref
     static constexpr int kTotal = kWarps + kPartBytes + kInt + kDbl + kScan + kByte;
 };
@@ -176,6 +176,8 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_batched_kernel(BatchArgs A)
     double *s_tab = s_beta + kBatchMaxInst;
     int32_t *s_aptr = reinterpret_cast<int32_t *>(smem + L::kWarps + kPartBytes + L::kInt + L::kDbl);
     int32_t *s_rptr = s_aptr + (kBatchMaxInst + 1);
+    int32_t *s_arow = s_rptr + (kBatchMaxInst + 1);
+    int32_t *s_rrow = s_arow + (kBatchMaxInst + 1);
     int8_t *s_dec = reinterpret_cast<int8_t *>(smem + L::kWarps + kPartBytes + L::kInt + L::kDbl + L::kScan);
     int8_t *s_ref = s_dec + kBatchMaxInst;
 
@@ -272,6 +274,66 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_batched_kernel(BatchArgs A)
                 atomicAdd(gacc + 2 * (ilo + k), gv);
                 atomicAdd(gacc + 2 * (ilo + k) + 1, rv);
             }
+        }
+    };
+
+    // Pass over the rows of the instances counted in the prefix `pre` (rows
+    // numbered instance by instance): every warp takes an equal contiguous
+    // chunk and visits it 64 rows at a time, lane l taking rows l and l + 32
+    // so that two rows' loads are in flight together.  f(rowA, instA, okA,
+    // rowB, instB, okB, gA, rA, gB, rB) updates both rows and returns their
+    // gamma and rho shares, which are summed per run of one instance and
+    // added to gacc with one atomic per run.
+    auto act_pass = [&](const int32_t *pre, double *gacc, auto f) {
+        const int64_t tot = pre[ni];
+        const int64_t per = div_up(div_up(tot, nwarps), 64) * 64;
+        const int64_t a0 = min64(gwarp * per, tot), a1 = min64(a0 + per, tot);
+        int cur = a0 < a1 ? find_seg(pre, ni, a0) : 0;
+        double gsum = 0.0, rsum = 0.0;
+        for (int64_t g0 = a0; g0 < a1; g0 += 64) {
+            const int64_t glast = min64(g0 + 63, a1 - 1);
+            const bool uniform = glast < pre[cur + 1];
+            if (!uniform) {
+                const double gs = warp_sum(gsum), rsm = warp_sum(rsum);
+                if (lane == 0 && (gs != 0.0 || rsm != 0.0)) {
+                    atomicAdd(gacc + 2 * cur, gs);
+                    atomicAdd(gacc + 2 * cur + 1, rsm);
+                }
+                gsum = rsum = 0.0;
+            }
+            const int64_t aA = g0 + lane, aB = g0 + 32 + lane;
+            const bool okA = aA < a1, okB = aB < a1;
+            int iA = cur, iB = cur;
+            if (!uniform) {
+                if (okA)
+                    while (aA >= pre[iA + 1]) ++iA;
+                iB = iA;
+                if (okB)
+                    while (aB >= pre[iB + 1]) ++iB;
+            }
+            const int64_t rowA = okA ? s_irow[iA] + (aA - pre[iA]) : 0;
+            const int64_t rowB = okB ? s_irow[iB] + (aB - pre[iB]) : 0;
+            double gA = 0.0, rA = 0.0, gB = 0.0, rB = 0.0;
+            f(rowA, iA, okA, rowB, iB, okB, gA, rA, gB, rB);
+            if (uniform) {
+                gsum += gA + gB;
+                rsum += rA + rB;
+            } else {
+                if (okA && (gA != 0.0 || rA != 0.0)) {
+                    atomicAdd(gacc + 2 * iA, gA);
+                    atomicAdd(gacc + 2 * iA + 1, rA);
+                }
+                if (okB && (gB != 0.0 || rB != 0.0)) {
+                    atomicAdd(gacc + 2 * iB, gB);
+                    atomicAdd(gacc + 2 * iB + 1, rB);
+                }
+                while (glast >= pre[cur + 1]) ++cur;  // warp-uniform: from the old run
+            }
+        }
+        const double gs = warp_sum(gsum), rsm = warp_sum(rsum);
+        if (lane == 0 && (gs != 0.0 || rsm != 0.0)) {
+            atomicAdd(gacc + 2 * cur, gs);
+            atomicAdd(gacc + 2 * cur + 1, rsm);
         }
     };
 
@@ -467,57 +529,89 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_batched_kernel(BatchArgs A)
         const int n_act_slices =
             block_scan(ni, [&](int i) { return (s_dec[i] == 0 || s_dec[i] == 4) ? nsl(i) : 0; }, s_aptr, s_warp);
         const int n_ref_slices = block_scan(ni, [&](int i) { return s_ref[i] ? nsl(i) : 0; }, s_rptr, s_warp);
+        block_scan(ni, [&](int i) { return (s_dec[i] == 0 || s_dec[i] == 4) ? s_irow[i + 1] - s_irow[i] : 0; },
+                   s_arow, s_warp);
+        block_scan(ni, [&](int i) { return s_ref[i] ? s_irow[i + 1] - s_irow[i] : 0; }, s_rrow, s_warp);
         if (n_act_slices == 0) break;  // every instance has stopped (same in every CTA)
 
         // delta slot of kk + 1 was last read in the scalar step of kk - 1
         if (blockIdx.x == 0)
             for (int k = threadIdx.x; k < ni; k += blockDim.x) d_next[k] = 0.0;
 
-        // ---- P phase
-        row_pass(gr_next, [&](int64_t i, int inst, double &gi, double &ri) {
-            const int dec = s_dec[inst];
-            if (dec != 0 && dec != 4) return;
-            const bool flagged = rowflag[i] != 0;
-            const bool ref = s_ref[inst] != 0;
-            if (dec == 4) {
+        // ---- P phase over the rows of the instances that step or verify
+        act_pass(s_arow, gr_next, [&](int64_t iA, int instA, bool okA, int64_t iB, int instB, bool okB, double &gA,
+                                      double &rA, double &gB, double &rB) {
+            const int64_t rw[2] = {iA, iB};
+            const int in_[2] = {instA, instB};
+            const bool ok2[2] = {okA, okB};
+            float uu[2][3], ww[2][3], pp[2][3], ss[2][3];
+            double xx[2][3], rr[2][3];
+            // loads of both rows first
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (!ok2[h] || s_dec[in_[h]] != 0) continue;
+                const int64_t i = rw[h];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    uu[h][c] = __ldcg(u + 3 * i + c);
+                    ww[h][c] = __ldcg(w + 3 * i + c);
+                    pp[h][c] = p[3 * i + c];
+                    ss[h][c] = s[3 * i + c];
+                    xx[h][c] = x[3 * i + c];
+                    rr[h][c] = r[3 * i + c];
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (!ok2[h]) continue;
+                const int64_t i = rw[h];
+                const int inst = in_[h];
+                const int dec = s_dec[inst];
+                const bool flagged = rowflag[i] != 0;
+                if (dec == 4) {
+                    // verify: no Krylov step; only clear what receives atomics
+                    if (flagged) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            w[3 * i + c] = 0.0f;
+                            ax[3 * i + c] = 0.0;
+                        }
+                    }
+                    continue;
+                }
+                if (dec != 0) continue;
+                const bool ref = s_ref[inst] != 0;
+                const double alpha = s_alpha[inst];
+                const float beta32 = (float)s_beta[inst];
+                double rn[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float pn = fmaf(beta32, pp[h][c], uu[h][c]);
+                    const float sn = fmaf(beta32, ss[h][c], ww[h][c]);
+                    p[3 * i + c] = pn;
+                    s[3 * i + c] = sn;
+                    x[3 * i + c] = fma(alpha, (double)pn, xx[h][c]);
+                    rn[c] = fma(-alpha, (double)sn, rr[h][c]);
+                    r[3 * i + c] = rn[c];
+                }
                 if (flagged) {
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         w[3 * i + c] = 0.0f;
-                        ax[3 * i + c] = 0.0;
+                        if (ref) ax[3 * i + c] = 0.0;
                     }
                 }
-                return;
-            }
-            const double alpha = s_alpha[inst];
-            const float beta32 = (float)s_beta[inst];
-            double rr[3];
+                if (!ref) {
+                    float un[3];
+                    precond32(A.dinv32 + 9 * i, rn, un);
+                    double gi = 0.0, ri = 0.0;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float uu = __ldcg(u + 3 * i + c), ww = __ldcg(w + 3 * i + c);
-                const float pp = fmaf(beta32, p[3 * i + c], uu);
-                const float ss = fmaf(beta32, s[3 * i + c], ww);
-                p[3 * i + c] = pp;
-                s[3 * i + c] = ss;
-                x[3 * i + c] = fma(alpha, (double)pp, x[3 * i + c]);
-                rr[c] = fma(-alpha, (double)ss, r[3 * i + c]);
-                r[3 * i + c] = rr[c];
-            }
-            if (flagged) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    w[3 * i + c] = 0.0f;
-                    if (ref) ax[3 * i + c] = 0.0;
-                }
-            }
-            if (!ref) {
-                float uu[3];
-                precond32(A.dinv32 + 9 * i, rr, uu);
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    u[3 * i + c] = uu[c];
-                    gi = fma(rr[c], (double)uu[c], gi);
-                    ri = fma(rr[c], rr[c], ri);
+                    for (int c = 0; c < 3; ++c) {
+                        u[3 * i + c] = un[c];
+                        gi = fma(rn[c], (double)un[c], gi);
+                        ri = fma(rn[c], rn[c], ri);
+                    }
+                    if (h == 0) { gA = gi; rA = ri; } else { gB = gi; rB = ri; }
                 }
             }
         });
@@ -540,22 +634,43 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_batched_kernel(BatchArgs A)
                 bsl::spmv<double, false, K>(wbuf, ql, cn, x, ax, rowflag, join, lane);
             }
             if (!grid_sync(count, nblocks, epoch, A.status)) { ok = false; break; }
-            row_pass(gr_next, [&](int64_t i, int inst, double &gi, double &ri) {
-                if (!s_ref[inst]) return;
-                double rr[3];
-                float uu[3];
+            act_pass(s_rrow, gr_next, [&](int64_t iA, int instA, bool okA, int64_t iB, int instB, bool okB,
+                                          double &gA, double &rA, double &gB, double &rB) {
+                const int64_t rw[2] = {iA, iB};
+                const bool ok2[2] = {okA, okB};
+                double axv[2][3], bv[2][3];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    rr[c] = fma(A.sign, A.b[3 * i + c], -__ldcg(ax + 3 * i + c));
-                    r[3 * i + c] = rr[c];
-                }
-                precond32(A.dinv32 + 9 * i, rr, uu);
+                for (int h = 0; h < 2; ++h) {
+                    if (!ok2[h]) continue;
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    u[3 * i + c] = uu[c];
-                    gi = fma(rr[c], (double)uu[c], gi);
-                    ri = fma(rr[c], rr[c], ri);
+                    for (int c = 0; c < 3; ++c) {
+                        axv[h][c] = __ldcg(ax + 3 * rw[h] + c);
+                        bv[h][c] = A.b[3 * rw[h] + c];
+                    }
                 }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (!ok2[h]) continue;
+                    const int64_t i = rw[h];
+                    double rn[3];
+                    float un[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        rn[c] = fma(A.sign, bv[h][c], -axv[h][c]);
+                        r[3 * i + c] = rn[c];
+                    }
+                    precond32(A.dinv32 + 9 * i, rn, un);
+                    double gi = 0.0, ri = 0.0;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        u[3 * i + c] = un[c];
+                        gi = fma(rn[c], (double)un[c], gi);
+                        ri = fma(rn[c], rn[c], ri);
+                    }
+                    if (h == 0) { gA = gi; rA = ri; } else { gB = gi; rB = ri; }
+                }
+                (void)instA;
+                (void)instB;
             });
         }
         if (!grid_sync(count, nblocks, epoch, A.status)) { ok = false; break; }
@@ -597,25 +712,25 @@ const void *kernel_ptr()
     return reinterpret_cast<const void *>(&pcg_batched_kernel<K>);
 }
 
-const int kVariants[kBatchVariants] = {3, 4, 5, 6};
+const int kVariants[kBatchVariants] = {4, 5, 6, 8};
 
 const void *variant_ptr(int v)
 {
     switch (v) {
-    case 0: return kernel_ptr<3>();
-    case 1: return kernel_ptr<4>();
-    case 2: return kernel_ptr<5>();
-    default: return kernel_ptr<6>();
+    case 0: return kernel_ptr<4>();
+    case 1: return kernel_ptr<5>();
+    case 2: return kernel_ptr<6>();
+    default: return kernel_ptr<8>();
     }
 }
 
 int variant_smem(int v)
 {
     switch (v) {
-    case 0: return Layout<3>::kTotal;
-    case 1: return Layout<4>::kTotal;
-    case 2: return Layout<5>::kTotal;
-    default: return Layout<6>::kTotal;
+    case 0: return Layout<4>::kTotal;
+    case 1: return Layout<5>::kTotal;
+    case 2: return Layout<6>::kTotal;
+    default: return Layout<8>::kTotal;
     }
 }
 

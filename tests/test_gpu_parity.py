@@ -330,3 +330,39 @@ def test_strain_tags_match_oracle(amp):
     assert np.array_equal(got, ref)
     if amp == 8e-6:  # a mix of protected and collapsible edges
         assert 0 < (ref == 0).sum() < ref.size
+
+
+@pytest.mark.parametrize("case", ["unit_cube", "domino_2x2"])
+def test_affine_embedding_matches_oracle(case):
+    # Sec. 4.2, Eq. 4: aggregates of more than 32 fine nodes get 12 DoF; the
+    # expanded Galerkin system, its gradient, solve and prolongation against
+    # the oracle's explicit P^T H P
+    from oracle import affine
+    import scipy.sparse as sps
+    if case == "unit_cube":
+        sc = scenes.unit_cube(seed=1001)
+    else:
+        sc = scenes.domino_grid(seed=1002, gx=2, gy=2, n_pairs=2000)
+    lab, nc = oracle.labels(sc.n, sc.edges, sc.tags)
+    pl, P, Hc, gc = affine.coarse_system(sc, lab, nc, threshold=32)
+    assert pl["affine"].any() and (~pl["affine"]).any()
+    ds = agipc.DeviceScene(sc)
+    ctx = ds.context()
+    st = agipc.AffineStep(ctx, ds, sc.meta["X_rest"], tol=1e-10, threshold=32)
+    st.run()
+    rc = ctx.status()
+    got = st.host()
+    ctx.close()
+    assert rc == 0, rc
+    assert np.array_equal(got["labels"], lab)
+    assert got["n_rows"] == pl["n_rows"]
+    assert np.array_equal(got["coarse_base"], pl["base"])
+    assert np.array_equal(got["coarse_k"], np.where(pl["affine"], 4, 1))
+    nr = pl["n_rows"]
+    H_gpu = sps.bsr_matrix((got["a_val"], got["a_col"], got["a_row_ptr"]), shape=(3 * nr, 3 * nr)).toarray()
+    H_ref = Hc.toarray()
+    assert np.abs(H_gpu - H_ref).max() <= 1e-11 * np.abs(H_ref).max()
+    assert np.abs(got["a_gc"].reshape(-1) - gc).max() <= 1e-11 * np.abs(gc).max()
+    y = got["y"].reshape(-1)
+    assert np.linalg.norm(H_ref @ y + gc) <= 1.05e-10 * np.linalg.norm(gc)
+    assert np.abs(got["dx"].reshape(-1) - P @ y).max() <= 1e-13 * np.abs(P @ y).max()
