@@ -44,6 +44,24 @@ def _dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(values, ws: int, device):
+    """Element-wise maximum of per-rank floats over all ranks (the job's
+    time is its slowest replica's); the identity on one rank."""
+    if ws == 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def replica_throughput(ws: int, units_per_rank: int, seconds: float) -> float:
+    """Whole-job throughput of ws independent replicas that each processed
+    units_per_rank units, timed by the slowest one."""
+    return ws * units_per_rank / seconds
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -246,10 +264,7 @@ def run_ours(args):
         batched = batched_form(dev, steps=min(args.steps, 10), peak_gbs=_peaks()[0])
 
     # ---- max over ranks
-    if ws > 1:
-        t = torch.tensor([total_s, e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s, e2e_s = float(t[0]), float(t[1])
+    total_s, e2e_s = max_over_ranks([total_s, e2e_s], ws, dev)
 
     if rank == 0:
         n_c, nnz_c, iters = res["n_c"], res["col"].size, res["iters"]
@@ -262,7 +277,8 @@ def run_ours(args):
         fine_iters, fine_nnz = fres["iters"], fres["col"].size
         fine_pcg_bytes = fine_iters * pcg_bytes_per_iter(fine_nnz, sc.n)
         out = {
-            "metric": METRIC, "value": ws * args.steps / total_s, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "metric": METRIC, "value": replica_throughput(ws, args.steps, total_s), "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_fine": sc.n, "n_pairs": sc.n_pairs, "fine_upper_nnzb": sc.nnzb,
@@ -287,7 +303,7 @@ def run_ours(args):
                          "fp64_tflops_pcg_algorithmic": fine_iters * pcg_flops_per_iter(fine_nnz, sc.n) /
                                                          (float(np.median(fine_ms)) / 1e3) / 1e12,
                          "speedup_of_coarsened": float(np.median(fine_ms)) / (1e3 * total_s / args.steps)},
-            "e2e": {"value": ws * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": {"value": replica_throughput(ws, e2e_steps, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": sum(KERNELS_PER_STEP.values()) * args.steps,
             "clocks": clocks,
             "precision_form": prec,
@@ -442,14 +458,14 @@ def differentiation_form(dev, steps: int):
     return out
 
 
-def batched_form(dev, steps: int, peak_gbs: float):
+def batched_form(dev, steps: int, peak_gbs: float, n_inst: int = 256):
     """Time the batched form: 256 uneven instances (2k-60k vertices) in one
     CUDA-graph replay of aggregate -> offsets -> mixed assembly -> batched
     PCG -> prolongation, with the autotuned slice width."""
     import torch
     from paper_2605_04773_gb300 import agipc, scenes
     t0 = time.perf_counter()
-    batch = scenes.batch_instances()
+    batch = scenes.batch_instances(n_inst=n_inst)
     gen_s = time.perf_counter() - t0
     bd = agipc.BatchDevice(batch, dev)
     ctx = bd.context()
@@ -502,7 +518,7 @@ def batched_form(dev, steps: int, peak_gbs: float):
            "pcg_roofline": {"bound": "hbm", "algorithmic_bytes": alg_bytes, "achieved_gbs": alg_bytes / med_pcg / 1e6,
                             "peak_gbs": peak_gbs, "frac": alg_bytes / med_pcg / 1e6 / peak_gbs},
            "generator_s": gen_s, "graph": "one CUDA graph replay per batch",
-           "workload": "256 Kuhn-split hex grids, 2k-60k vertices log-uniform, random aspect, 30-90% collapsible, "
+           "workload": str(batch.n_inst) + " Kuhn-split hex grids, 2k-60k vertices log-uniform, random aspect, 30-90% collapsible, "
                        "0-5% of vertices in PT barrier stencils; FP32 blocks, FP64 accumulation, tol 1e-6"}
     ctx.close()
     return out
@@ -551,6 +567,24 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def run_one_form(args):
+    """One form on one GPU, its JSON object on stdout: the command the kernel
+    profiles under profiles/ are captured with."""
+    import torch
+    from paper_2605_04773_gb300 import build
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    steps = max(1, args.steps)
+    if args.form == "precision":
+        out = precision_form(ctx_factory=lambda d: d.context(), dev=dev, steps=steps)
+    elif args.form == "differentiation":
+        out = differentiation_form(dev, steps=steps)
+    else:
+        out = batched_form(dev, steps=steps, peak_gbs=_peaks()[0], n_inst=args.batch_instances)
+    print(json.dumps({"form": args.form, **out}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -559,8 +593,13 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-forms", action="store_true", help="only the headline step (profiling runs)")
+    ap.add_argument("--form", choices=["precision", "differentiation", "batched"], default=None,
+                    help="run one form alone and print its JSON object (profiling runs)")
+    ap.add_argument("--batch-instances", type=int, default=256, help="instances of the batched form with --form")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.form is not None:
+        run_one_form(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
