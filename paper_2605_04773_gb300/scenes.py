@@ -586,6 +586,32 @@ def diff_problem(sc: Scene) -> dict:
                 g_pairs=m["g_pairs"], x_target=x_target)
 
 
+def newton_problem(sc: Scene, v_drop: float = 1.0, bump_speed: float = 2.0, bump_radius: float = 0.15) -> dict:
+    """The Newton-loop workload from a scene (normally ``diff_grid``): the body
+    at its rest shape (x = X_rest) moving down at v_drop m/s, plus a
+    compressive velocity bump of bump_speed m/s (Gaussian, radius
+    bump_radius) at the top corner of the bounding box, as after an impact
+    there.  x_hat = x + h v + h^2 gravity enters the solver as the constant
+    linear term g_extra = -(M/h^2) h v (the fine system's inertia term uses
+    X_rest + h^2 gravity); x_last = x - h v are the previous time step's
+    positions, the reference of the first iteration's strain-increment
+    tags."""
+    pr = diff_problem(sc)
+    X = np.asarray(pr["X_rest"], dtype=np.float64)
+    h = pr["h"]
+    corner = X.max(0)
+    r2 = np.sum((X - corner) ** 2, axis=1)
+    v = np.zeros_like(X)
+    v[:, 2] = -v_drop - bump_speed * np.exp(-r2 / (2.0 * bump_radius ** 2))
+    pr = dict(pr)
+    pr["x"] = X.copy()
+    pr["x_last"] = X - h * v
+    pr["v"] = v
+    pr["g_extra"] = -(pr["mass_h2"] * h)[:, None] * v
+    pr["g_pairs"] = None
+    return pr
+
+
 # ----------------------------------------------------------------------------
 # Batched form: many independent meshes of uneven sizes
 # ----------------------------------------------------------------------------
