@@ -255,13 +255,15 @@ def run_ours(args):
     # ---- precision form (FP32 blocks/SpMV/preconditioner, FP64 dots and
     # residual replacement every 20 iterations, small-gap stencils in FP64) on
     # the same workload with 1% of the barrier gaps redrawn below 0.05 dhat
-    prec = diff = batched = None
+    prec = diff = batched = newton = None
     if not args.skip_forms:
         prec = precision_form(ctx_factory=lambda d: d.context(), dev=dev, steps=min(args.steps, 20))
         # ---- differentiation form (forward step + adjoint + per-tet VJP)
         diff = differentiation_form(dev, steps=min(args.steps, 10))
         # ---- batched form (256 uneven instances, one graph replay)
         batched = batched_form(dev, steps=min(args.steps, 10), peak_gbs=_peaks()[0])
+        # ---- the Newton loop with backtracking (fine assembly to line search)
+        newton = newton_form(dev, steps=min(args.steps, 5))
 
     # ---- max over ranks
     total_s, e2e_s = max_over_ranks([total_s, e2e_s], ws, dev)
@@ -309,6 +311,7 @@ def run_ours(args):
             "precision_form": prec,
             "differentiation_form": diff,
             "batched_form": batched,
+            "newton_form": newton,
             "wall_s_timed_region": t_wall,
         }
         if ws == 1 and not args.no_cpu_baseline:
@@ -458,6 +461,54 @@ def differentiation_form(dev, steps: int):
     return out
 
 
+def newton_form(dev, steps: int):
+    """Time the coarsened Newton loop with backtracking (Algorithm 1's inner
+    loop) on the 46^3 StVK grid after an impact: per iteration fine
+    assembly, strain-increment tags, labels, coarse assembly, PCG to 1e-3,
+    prolongation, 10 post-coarsening PCG iterations, |d|_inf and the line
+    search's energy evaluations, until |d|_inf / h <= 1e-3 l (the paper's
+    tolerances).  One timed step = one time step's whole Newton loop."""
+    import torch
+    from paper_2605_04773_gb300 import agipc, scenes
+    sc = scenes.diff_grid()
+    pr = scenes.newton_problem(sc)
+    dp = agipc.DiffDeviceProblem(pr, dev)
+    ctx = dp.context()
+    E = torch.tensor(pr["E"], dtype=torch.float64, device=dev)
+    X = torch.tensor(pr["X_rest"], dtype=torch.float64, device=dev)
+    x_last = torch.tensor(pr["x_last"], dtype=torch.float64, device=dev)
+    sol = agipc.NewtonSolver(ctx, dp, E, X, x_last)
+    for _ in range(2):
+        res = sol.run()
+    stream = torch.cuda.current_stream(dev)
+    l2 = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    ms, its = [], []
+    for _ in range(steps):
+        l2.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        res = sol.run()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        ms.append(a.elapsed_time(b))
+        its.append(res["iterations"])
+    ctx.check()
+    hist = res["history"]
+    med = float(np.median(ms))
+    out = {"value": float(np.sum(its)) / (float(np.sum(ms)) / 1e3), "unit": "Newton iterations/s",
+           "time_steps_per_s": 1e3 / med, "ms_per_time_step": med, "newton_iterations": int(its[-1]),
+           "ms_per_newton_iteration": med / its[-1], "converged": bool(res["converged"]),
+           "n_c_per_iteration": [h_["n_c"] for h_ in hist], "alpha_per_iteration": [h_["alpha"] for h_ in hist],
+           "line_search_trials": int(sum(h_["trials"] for h_ in hist)),
+           "coarse_pcg_iters": [h_["coarse_iters"] for h_ in hist],
+           "dnorm_over_h": [h_["dnorm"] / dp.h for h_ in hist], "eps_d": sol.eps_d,
+           "workload": "46^3 Kuhn grid (103,823 vertices, 584,016 tets), log-normal E around 1e5 Pa, at rest "
+                       "shape falling at 1 m/s with a 2 m/s compressive bump at one corner; threshold 5e-5, "
+                       "PCG 1e-3, 10 post-coarsening iterations, eps_d = 1e-3 l, FP64"}
+    ctx.close()
+    return out
+
+
 def batched_form(dev, steps: int, peak_gbs: float, n_inst: int = 256):
     """Time the batched form: 256 uneven instances (2k-60k vertices) in one
     CUDA-graph replay of aggregate -> offsets -> mixed assembly -> batched
@@ -580,6 +631,8 @@ def run_one_form(args):
         out = precision_form(ctx_factory=lambda d: d.context(), dev=dev, steps=steps)
     elif args.form == "differentiation":
         out = differentiation_form(dev, steps=steps)
+    elif args.form == "newton":
+        out = newton_form(dev, steps=steps)
     else:
         out = batched_form(dev, steps=steps, peak_gbs=_peaks()[0], n_inst=args.batch_instances)
     print(json.dumps({"form": args.form, **out}))
@@ -593,7 +646,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-forms", action="store_true", help="only the headline step (profiling runs)")
-    ap.add_argument("--form", choices=["precision", "differentiation", "batched"], default=None,
+    ap.add_argument("--form", choices=["precision", "differentiation", "batched", "newton"], default=None,
                     help="run one form alone and print its JSON object (profiling runs)")
     ap.add_argument("--batch-instances", type=int, default=256, help="instances of the batched form with --form")
     args = ap.parse_args()

@@ -419,6 +419,35 @@ int64_t agipc_stvk_workspace_bytes(int64_t n_tets);
 int agipc_aggregate_static(void *cuda_stream, int32_t n_fine, int64_t n_edges, const int32_t *edges,
                            const uint8_t *tags, int32_t *labels, int32_t *n_coarse_dev, uint32_t *status_dev);
 
+/*
+ * Incremental potential of the StVK problem at a trial point (Eq. 1 divided
+ * by dt^2, without barrier or friction terms; the quantity the backtracking
+ * line search of Algorithm 1 compares, E(x) < E_prev):
+ *   x = x0 + alpha d   (product and sum each rounded once; d may be NULL: x = x0)
+ *   E(x) = sum_i mass_h2[i] / 2 |x_i - X_rest_i - xhat_shift|^2
+ *        + sum_e V_e (mu_e |G_e|_F^2 + lam_e / 2 tr(G_e)^2) + g_extra . x
+ * with G_e = (F^T F - I) / 2, F = Ds Dm^-1, V_e = |det Dm| / 6 and the Lame
+ * parameters of E[e] and nu, i.e. the energy whose gradient and Hessian
+ * agipc_fine_assemble_stvk sums (same arguments, same meaning).
+ *   tets [n_tets][4], X_rest, x0, d [n_fine][3], E [n_tets], mass_h2 [n_fine],
+ *   xhat_shift [3] host, g_extra [n_fine][3] or NULL
+ *   x_out [n_fine][3] or NULL: receives x; must not overlap x0 or d
+ *   energy_dev (device double) out
+ * The sum is deterministic (same inputs and device: same bits).  A tet
+ * index out of range sets AGIPC_ERR_BAD_INDEX and the tet is skipped.
+ * Calls on one context are serialized by its stream; the reduction scratch
+ * lives in the context.
+ */
+int agipc_stvk_energy(agipc_ctx *ctx, int32_t n_fine, int64_t n_tets, const int32_t *tets, const double *X_rest,
+                      const double *x0, const double *d, double alpha, const double *xhat_shift, const double *E,
+                      double nu, const double *mass_h2, const double *g_extra, double *x_out, double *energy_dev);
+
+/*
+ * out_dev = max_k |v[k]| over n doubles (0 for n = 0): the Newton loop's
+ * stopping test ||d||_inf / dt <= eps_d (Algorithm 1).  Exact (no rounding).
+ */
+int agipc_max_abs(agipc_ctx *ctx, int64_t n, const double *v, double *out_dev);
+
 /* Synchronize the context's stream; return (and clear) the first device-side
  * error recorded since the last call, or AGIPC_OK. */
 int agipc_status(agipc_ctx *ctx);

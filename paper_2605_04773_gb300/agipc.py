@@ -86,13 +86,15 @@ def load():
                                           P, P, P]
     lib.agipc_prolongate_affine.argtypes = [P, i32, P, P, P, P, P, P, P]
     lib.agipc_pcg_batched.argtypes = [P, i32, P, i32, P, P, P, P, P, P, P, ctypes.POINTER(_PcgOptions), i32, i32, P, P]
+    lib.agipc_stvk_energy.argtypes = [P, i32, i64, P, P, P, P, f64, D3, P, f64, P, P, P, P]
+    lib.agipc_max_abs.argtypes = [P, i64, P, P]
     lib.agipc_status_string.argtypes = [ctypes.c_int]
     lib.agipc_status_string.restype = ctypes.c_char_p
     for name in ("agipc_create", "agipc_destroy", "agipc_set_stream", "agipc_aggregate", "agipc_assemble_coarse",
                  "agipc_pcg", "agipc_prolongate", "agipc_status", "agipc_aggregate_static",
                  "agipc_assemble_coarse_mixed", "agipc_pcg_mixed", "agipc_prolongate_add", "agipc_fine_assemble_stvk",
                  "agipc_restrict", "agipc_stvk_vjp", "agipc_batch_coarse_offsets", "agipc_pcg_batched", "agipc_strain_tags", "agipc_affine_plan", "agipc_assemble_affine",
-                 "agipc_prolongate_affine"):
+                 "agipc_prolongate_affine", "agipc_stvk_energy", "agipc_max_abs"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -242,6 +244,18 @@ def agipc_strain_tags(ctx: Context, n_fine: int, tets, X_rest, x_prev, x_cur, th
     _check(load().agipc_strain_tags(ctx.handle, int(n_fine), int(tets.shape[0]), _ptr(tets), _ptr(X_rest),
                                     _ptr(x_prev), _ptr(x_cur), float(threshold), _ptr(fine_row_ptr), _ptr(fine_col),
                                     int(fine_col.shape[0]), int(tags.shape[0]), _ptr(tags)), "agipc_strain_tags")
+
+
+def agipc_stvk_energy(ctx: Context, n_fine: int, tets, X_rest, x0, d, alpha: float, xhat_shift, E, nu: float,
+                      mass_h2, g_extra, x_out, energy_dev):
+    shift = (ctypes.c_double * 3)(*[float(v) for v in xhat_shift])
+    _check(load().agipc_stvk_energy(ctx.handle, int(n_fine), int(tets.shape[0]), _ptr(tets), _ptr(X_rest), _ptr(x0),
+                                    _ptr(d), float(alpha), shift, _ptr(E), float(nu), _ptr(mass_h2), _ptr(g_extra),
+                                    _ptr(x_out), _ptr(energy_dev)), "agipc_stvk_energy")
+
+
+def agipc_max_abs(ctx: Context, v, out_dev):
+    _check(load().agipc_max_abs(ctx.handle, int(v.numel()), _ptr(v), _ptr(out_dev)), "agipc_max_abs")
 
 
 BATCH_MAX_INSTANCES = 512
@@ -471,7 +485,9 @@ class DiffDeviceProblem:
         self.mass_h2 = t(problem["mass_h2"], torch.float64)
         self.pair_idx = t(np.asarray(problem["pair_idx"]).reshape(-1, 4), torch.int32)
         self.pair_blk = t(np.asarray(problem["pair_blk"]).reshape(-1, 90), torch.float64)
-        gp = problem.get("g_pairs")
+        gp = problem.get("g_extra")
+        if gp is None:
+            gp = problem.get("g_pairs")
         self.g_extra = None if gp is None or not np.any(gp) else t(gp, torch.float64)
         self.xhat_shift = tuple(self.h * self.h * gv for gv in GRAVITY)
 
@@ -568,6 +584,143 @@ class CoarsenedStepFunction(torch.autograd.Function):
 def coarsened_step(E, X_rest, step: DiffStep):
     """Differentiable coarsened Newton step (see CoarsenedStepFunction)."""
     return CoarsenedStepFunction.apply(E, X_rest, step)
+
+
+class NewtonSolver:
+    """The coarsened Newton loop with backtracking line search (the inner
+    loop of Algorithm 1) on the StVK problem without contact.  Per
+    iteration, on the device: fine assembly (agipc_fine_assemble_stvk), tags
+    from the Green-strain increment against the previous iterate
+    (agipc_strain_tags; at the first iteration against x_last, the previous
+    time step), labels, coarse assembly, coarse PCG, prolongation,
+    post-coarsening (at most post_iters fine PCG iterations from d) and
+    |d|_inf; then alpha = 1, 1/2, ... until E(x_prev + alpha d) <
+    E_prev (agipc_stvk_energy).  The loop stops when |d|_inf / h <= eps_d
+    (default 1e-3 l, l the rest bounding-box diagonal).  The host reads two
+    scalars per line-search trial and the status once per iteration."""
+
+    def __init__(self, ctx: Context, dp: DiffDeviceProblem, E, X_rest, x_last, threshold: float = 5e-5,
+                 tol: float = 1e-3, eps_d: float = None, max_newton: int = 50, post_iters: int = 10,
+                 max_halvings: int = 30, max_iter: int = 100000):
+        dev = dp.x.device
+        n, cap = dp.n, dp.capacity
+        i32 = dict(device=dev, dtype=torch.int32)
+        f64 = dict(device=dev, dtype=torch.float64)
+        self.ctx, self.dp = ctx, dp
+        self.E = E.contiguous()
+        self.X_rest = X_rest.contiguous()
+        self.threshold, self.tol, self.max_newton = float(threshold), float(tol), int(max_newton)
+        self.post_iters, self.max_halvings, self.max_iter = int(post_iters), int(max_halvings), int(max_iter)
+        if eps_d is None:
+            ext = (self.X_rest.max(0).values - self.X_rest.min(0).values).cpu().numpy()
+            eps_d = 1e-3 * float(np.linalg.norm(ext))
+        self.eps_d = float(eps_d)
+        self.x_start = dp.x
+        self.x = torch.empty(n, 3, **f64)
+        self.x_trial = torch.empty(n, 3, **f64)
+        self.x_before = torch.empty(n, 3, **f64)
+        self.x_last = x_last.contiguous()
+        self.fine_val = torch.empty(dp.col.shape[0], 9, **f64)
+        self.g = torch.empty(n, 3, **f64)
+        self.tags = torch.empty(dp.edges.shape[0], device=dev, dtype=torch.uint8)
+        self.labels = torch.empty(n, **i32)
+        self.n_c = torch.zeros(1, **i32)
+        self.row_ptr = torch.empty(n + 1, **i32)
+        self.col = torch.empty(cap, **i32)
+        self.val = torch.empty(cap, 9, **f64)
+        self.nnz = torch.zeros(1, **i32)
+        self.g_c = torch.empty(n, 3, **f64)
+        self.dinv = torch.empty(n, 9, **f64)
+        self.y = torch.empty(n, 3, **f64)
+        self.d = torch.empty(n, 3, **f64)
+        self.iters = torch.zeros(1, **i32)
+        self.relres = torch.zeros(1, **f64)
+        # the fine system in full storage for the post-coarsening (identity labels)
+        self.ident = torch.arange(n, **i32)
+        self.n_ident = torch.full((1,), n, **i32)
+        self.f_row_ptr = torch.empty(n + 1, **i32)
+        self.f_col = torch.empty(cap, **i32)
+        self.f_val = torch.empty(cap, 9, **f64)
+        self.f_nnz = torch.zeros(1, **i32)
+        self.f_g = torch.empty(n, 3, **f64)
+        self.f_dinv = torch.empty(n, 9, **f64)
+        self.p_iters = torch.zeros(1, **i32)
+        self.p_relres = torch.zeros(1, **f64)
+        self.scal = torch.zeros(2, **f64)       # [energy, |d|_inf]
+        self.workspace = stvk_workspace(dp.tets.shape[0], dev)
+        self.history = []
+
+    def energy(self, x0, d=None, alpha: float = 0.0, x_out=None) -> float:
+        dp = self.dp
+        agipc_stvk_energy(self.ctx, dp.n, dp.tets, self.X_rest, x0, d, alpha, dp.xhat_shift, self.E, dp.nu,
+                          dp.mass_h2, dp.g_extra, x_out, self.scal[:1])
+        return float(self.scal[0].item())
+
+    def direction(self, x, x_before):
+        """Enqueue the steps from the fine assembly at x to d (post-coarsened)
+        and |d|_inf; the coarse solve's status is checked on the host."""
+        dp, ctx = self.dp, self.ctx
+        agipc_fine_assemble_stvk(ctx, dp.n, dp.tets, self.X_rest, x, dp.xhat_shift, self.E, dp.nu, dp.mass_h2,
+                                 dp.g_extra, dp.row_ptr, dp.col, self.fine_val, self.g, self.workspace)
+        agipc_strain_tags(ctx, dp.n, dp.tets, self.X_rest, x_before, x, self.threshold, dp.row_ptr, dp.col, self.tags)
+        agipc_aggregate(ctx, dp.n, dp.edges, self.tags, self.labels, self.n_c)
+        agipc_assemble_coarse(ctx, dp.n, self.labels, self.n_c, dp.row_ptr, dp.col, self.fine_val, dp.pair_idx,
+                              dp.pair_blk, self.g, self.row_ptr, self.col, self.val, self.nnz, self.g_c, self.dinv)
+        agipc_pcg(ctx, dp.n, self.n_c, self.row_ptr, self.col, self.val, self.dinv, self.g_c, self.y, self.tol,
+                  self.max_iter, -1, self.iters, self.relres)
+        agipc_prolongate(ctx, dp.n, self.labels, self.y, self.d)
+        if self.post_iters > 0:
+            agipc_assemble_coarse(ctx, dp.n, self.ident, self.n_ident, dp.row_ptr, dp.col, self.fine_val, dp.pair_idx,
+                                  dp.pair_blk, self.g, self.f_row_ptr, self.f_col, self.f_val, self.f_nnz, self.f_g,
+                                  self.f_dinv)
+            ctx.check()
+            agipc_pcg(ctx, dp.n, self.n_ident, self.f_row_ptr, self.f_col, self.f_val, self.f_dinv, self.f_g, self.d,
+                      self.tol, self.post_iters, -1, self.p_iters, self.p_relres, use_x0=True)
+            ctx.check(allow=(OK, ERR_NOT_CONVERGED))   # the post-coarsening is capped on purpose
+        else:
+            ctx.check()
+        agipc_max_abs(ctx, self.d, self.scal[1:])
+
+    def run(self, keep_labels: bool = False):
+        """The whole loop from the problem's x.  Returns dict(x, history,
+        converged, stalled, iterations)."""
+        dp = self.dp
+        self.x.copy_(self.x_start)
+        self.x_before.copy_(self.x_last)
+        e_prev = self.energy(self.x)
+        self.history = []
+        converged = stalled = False
+        for _ in range(self.max_newton):
+            self.direction(self.x, self.x_before)
+            dnorm = float(self.scal[1].item())
+            alpha, e_new, trials = 1.0, None, 0
+            for k in range(self.max_halvings + 1):
+                e = self.energy(self.x, self.d, alpha, self.x_trial)
+                trials = k + 1
+                if e < e_prev:
+                    e_new = e
+                    break
+                alpha *= 0.5
+            rec = dict(e_prev=e_prev, n_c=int(self.n_c.item()), coarse_iters=int(self.iters.item()),
+                       post_iters=int(self.p_iters.item()) if self.post_iters > 0 else 0, dnorm=dnorm,
+                       alpha=alpha if e_new is not None else None, trials=trials, e_new=e_new)
+            if keep_labels:
+                rec["labels"] = self.labels.cpu().numpy()
+                rec["d"] = self.d.cpu().numpy()
+            self.history.append(rec)
+            if e_new is None:
+                converged = dnorm / dp.h <= self.eps_d
+                stalled = not converged
+                break
+            # rotate: x_before <- x, x <- x_trial
+            self.x_before, self.x, self.x_trial = self.x, self.x_trial, self.x_before
+            e_prev = e_new
+            if dnorm / dp.h <= self.eps_d:
+                converged = True
+                break
+        self.ctx.check()
+        return dict(x=self.x, history=self.history, converged=converged, stalled=stalled,
+                    iterations=len(self.history))
 
 
 # ---------------------------------------------------------------------------

@@ -76,7 +76,14 @@ struct agipc_ctx {
     // batched PCG
     double *batch_acc;                // [6 * kBatchMaxInst] per-instance sums
     int batch_grid[kBatchVariants];   // cooperative grid of each slice-width variant
+
+    // deterministic reductions (energy): one partial per CTA, then the last
+    // CTA to arrive sums them in CTA order
+    double *red_part;                 // [kRedMaxCtas]
+    unsigned *red_ticket;             // [32]: [0] arrivals (reset by the last CTA)
 };
+
+constexpr int kRedMaxCtas = 1024;
 
 // --------------------------------------------------------------------------
 // memory-order helpers (gpu scope)

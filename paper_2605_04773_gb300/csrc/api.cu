@@ -54,6 +54,8 @@ void carve_all(agipc_ctx *c, char *base, size_t *total)
     c->pcg.partials = cv.take<double>(2 * (size_t)c->pcg.max_grid * 4);
     c->pcg.bar = cv.take<unsigned>(64);
     c->batch_acc = cv.take<double>(6 * (size_t)kBatchMaxInst);
+    c->red_part = cv.take<double>(kRedMaxCtas);
+    c->red_ticket = cv.take<unsigned>(32);
     *total = cv.off;
 }
 

@@ -74,7 +74,9 @@ def test_pure_inertia_newton_lands_on_x_hat():
     pr = _small()
     X = pr["X_rest"]
     E0 = np.zeros(pr["tets"].shape[0])
-    out = N.newton(pr, E0, X, pr["x_last"], threshold=0.0, tol=1e-14, post_iters=0)
+    # a noisy previous step: every tet's strain increment is nonzero
+    x_last = pr["x"] + 1e-3 * np.random.default_rng(5).standard_normal(pr["x"].shape)
+    out = N.newton(pr, E0, X, x_last, threshold=0.0, tol=1e-14, post_iters=0)
     x_hat = X + pr["h"] * pr["v"] + pr["h"] ** 2 * GRAVITY
     assert out["converged"]
     assert len(out["history"]) == 2
@@ -107,7 +109,8 @@ def test_full_resolution_newton_is_plain_newton(post):
     # system is the fine one and the loop is plain Newton with PCG; the step
     # then solves H d = -g to the PCG tolerance
     pr = _small()
-    out = N.newton(pr, pr["E"], pr["X_rest"], pr["x_last"], threshold=0.0, tol=1e-12, post_iters=post, max_newton=1)
+    x_last = pr["x"] + 1e-3 * np.random.default_rng(6).standard_normal(pr["x"].shape)
+    out = N.newton(pr, pr["E"], pr["X_rest"], x_last, threshold=0.0, tol=1e-12, post_iters=post, max_newton=1)
     h0 = out["history"][0]
     assert h0["n_c"] == pr["n"]
     assert np.array_equal(h0["labels"], np.arange(pr["n"]))
