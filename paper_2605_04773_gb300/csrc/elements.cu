@@ -197,17 +197,29 @@ __host__ __device__ constexpr int pk(int i, int j)
     return i <= j ? 9 * i - (i * (i - 1)) / 2 + (j - i) : 9 * j - (j * (j - 1)) / 2 + (i - j);
 }
 
-// Reduced Hessian M (9x9, index 3k+c), FP32, packed upper.
+// Reduced Hessian M (9x9, index 3k+c), packed upper, formed in FP32 from
+// the FP64 invariants (it only feeds the FP32 classification).
 __device__ __forceinline__ void reduced_m32(const Tet &t, double mu, double lam, float A[45])
 {
+    float Y[3][3], FF[3][3], om[3][3], sv[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            Y[i][j] = (float)t.Y[i][j];
+            FF[i][j] = (float)t.FFt[i][j];
+            om[i][j] = (float)t.om[i][j];
+            sv[i][j] = (float)(t.V * t.s[i][j]);
+        }
+    const float vm = (float)(t.V * mu), vl = (float)(t.V * lam);
 #pragma unroll
     for (int r = 0; r < 9; ++r)
 #pragma unroll
         for (int q = r; q < 9; ++q) {
             const int k = r / 3, c = r % 3, l = q / 3, d = q % 3;
-            double v = mu * t.Y[l][c] * t.Y[k][d] + mu * t.FFt[c][d] * t.om[k][l] + lam * t.Y[k][c] * t.Y[l][d];
-            if (c == d) v += t.s[k][l];
-            A[pk(r, q)] = (float)(t.V * v);
+            float v = vm * (Y[l][c] * Y[k][d] + FF[c][d] * om[k][l]) + vl * Y[k][c] * Y[l][d];
+            if (c == d) v += sv[k][l];
+            A[pk(r, q)] = v;
         }
 }
 
@@ -315,38 +327,67 @@ struct Slots {
     __device__ __forceinline__ double &raw(int s) const { return base[s * kRefineThreads + lane]; }
 };
 
-// FP64 refinement of a tet's FP32 eigenbasis.  Recomputes the FP32
-// decomposition, orders the flagged eigenvalues first, re-orthonormalises
-// U in FP64 (modified Gram-Schmidt), forms A = U^T M U and runs FP64
-// Jacobi sweeps over every pair (p, q) with p < m_warp (all pairs when
-// all_pairs), m_warp the warp's largest flagged count (the worklist is
-// ordered by flagged count, so a warp's tets mostly share it).  Returns
-// m_warp.
-__device__ int refine64(const Tet &t, double mu, double lam, const Slots &sl, bool all_pairs)
+// FP32 eigenpairs of a flagged tet's reduced Hessian, written by pass 1 and
+// read by pass 2: one 368-byte record per tet (92 floats, 16-byte aligned):
+// the 9 eigenvalues, then eigenvector i's rows at 9 + 9 i + r, then 2 pad.
+// A flagged tet's record is written whole (full sectors, no read-fill).
+constexpr int kEigRec = 92;
+
+struct EigStore {
+    float *base;
+    int64_t nt;
+    __device__ __forceinline__ const float &val(int64_t e, int i) const { return base[e * kEigRec + i]; }
+    __device__ __forceinline__ const float &vec(int64_t e, int r, int i) const
+    {
+        return base[e * kEigRec + 9 + 9 * i + r];
+    }
+};
+
+__device__ __forceinline__ void store_eig(const EigStore &es, int64_t e, const float A[45], const float U[9][9])
 {
-    float A32[45], U32[9][9];
-    reduced_m32(t, mu, lam, A32);
-    jacobi9f(A32, U32);
+    float rec[kEigRec];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        rec[i] = A[pk(i, i)];
+#pragma unroll
+        for (int r = 0; r < 9; ++r) rec[9 + 9 * i + r] = U[r][i];
+    }
+    rec[90] = rec[91] = 0.f;
+    float4 *dst = reinterpret_cast<float4 *>(es.base + e * kEigRec);
+#pragma unroll
+    for (int q = 0; q < kEigRec / 4; ++q) dst[q] = make_float4(rec[4 * q], rec[4 * q + 1], rec[4 * q + 2], rec[4 * q + 3]);
+}
+
+// FP64 refinement of a tet's FP32 eigenbasis (the pairs pass 1 stored).
+// Orders the flagged eigenvalues first, re-orthonormalises U in FP64
+// (modified Gram-Schmidt), forms A = U^T M U and runs FP64 Jacobi sweeps
+// over every pair (p, q) with p < m_warp (all pairs when all_pairs),
+// m_warp the warp's largest flagged count (the worklist is ordered by
+// flagged count, so a warp's tets mostly share it).  Returns m_warp.
+__device__ int refine64(const Tet &t, double mu, double lam, const Slots &sl, bool all_pairs, const EigStore &es,
+                        int64_t e)
+{
     float big = 0.f;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) big = fmaxf(big, fabsf(A32[pk(i, i)]));
+    for (int i = 0; i < 9; ++i) big = fmaxf(big, fabsf(es.val(e, i)));
     // order: flagged eigenvalues first (stable in index), then the rest
     int nf = 0;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) nf += A32[pk(i, i)] <= kPdRel * big ? 1 : 0;
+    for (int i = 0; i < 9; ++i) nf += es.val(e, i) <= kPdRel * big ? 1 : 0;
     int fi = 0, pi = nf;
-#pragma unroll
+#pragma unroll 1
     for (int i = 0; i < 9; ++i) {
-        const bool f = A32[pk(i, i)] <= kPdRel * big;
+        const bool f = es.val(e, i) <= kPdRel * big;
         const int slot = f ? fi : pi;
         fi += f ? 1 : 0;
         pi += f ? 0 : 1;
 #pragma unroll
-        for (int r = 0; r < 9; ++r) sl.u(r, slot) = (double)U32[r][i];
+        for (int r = 0; r < 9; ++r) sl.u(r, slot) = (double)es.vec(e, r, i);
     }
     const unsigned mask = __activemask();
     const int m_warp = all_pairs ? 8 : __reduce_max_sync(mask, nf);
     // modified Gram-Schmidt in FP64
+#pragma unroll 1
     for (int j = 0; j < 9; ++j) {
         for (int i = 0; i < j; ++i) {
             double d = 0.0;
@@ -364,6 +405,7 @@ __device__ int refine64(const Tet &t, double mu, double lam, const Slots &sl, bo
     }
     // A = U^T M U
     double scale = 0.0;
+#pragma unroll 1
     for (int j = 0; j < 9; ++j) {
         double v[9], mv[9];
 #pragma unroll
@@ -509,6 +551,14 @@ __device__ __forceinline__ int64_t flagged_total(const int32_t *hdr)
     return t;
 }
 
+// A load the compiler may not merge with an earlier one.
+__device__ __forceinline__ double ld_fresh(const double *p)
+{
+    double v;
+    asm volatile("ld.global.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+
 struct Shift3 {
     double v[3];
 };
@@ -547,7 +597,7 @@ __global__ void __launch_bounds__(128) elem_pass1_kernel(int32_t n, int64_t nt, 
                                                          const int32_t *__restrict__ col, int64_t nnzb,
                                                          const double *__restrict__ Xr, const double *__restrict__ xc,
                                                          const double *__restrict__ E, double nu, double *fine_val,
-                                                         double *g, int32_t *hdr, uint8_t *mcode,
+                                                         double *g, int32_t *hdr, uint8_t *mcode, EigStore es,
                                                          uint32_t *status)
 {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nt; e += (int64_t)gridDim.x * blockDim.x) {
@@ -609,6 +659,7 @@ __global__ void __launch_bounds__(128) elem_pass1_kernel(int32_t n, int64_t nt, 
                 reduced_m32(t, mu, lam, A32);
                 jacobi9f(A32, U32);
                 flag = flagged_count(A32);
+                if (flag > 0) store_eig(es, e, A32, U32);
             }
         }
         mcode[e] = (uint8_t)flag;
@@ -620,7 +671,7 @@ __global__ void __launch_bounds__(128) elem_pass1_kernel(int32_t n, int64_t nt, 
 __global__ void __launch_bounds__(kRefineThreads) elem_pass2_kernel(
     int32_t n, const int32_t *__restrict__ tets, const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
     int64_t nnzb, const double *__restrict__ Xr, const double *__restrict__ xc, const double *__restrict__ E, double nu,
-    double *fine_val, const int32_t *__restrict__ hdr, const int32_t *__restrict__ list, int64_t cap,
+    double *fine_val, const int32_t *__restrict__ hdr, const int32_t *__restrict__ list, int64_t cap, EigStore es,
     uint32_t *status)
 {
     __shared__ double sm[kRefineSlots * kRefineThreads];
@@ -636,7 +687,7 @@ __global__ void __launch_bounds__(kRefineThreads) elem_pass2_kernel(
         lame(E[e], nu, mu, lam);
         Tet t;
         tet_eval(X, x, mu, lam, t);
-        const int m_w = refine64(t, mu, lam, sl, false);
+        const int m_w = refine64(t, mu, lam, sl, false, es, e);
         // negative part of the flagged block; R_i = Q u_i (12 words) is
         // written downwards from the top slot once A has been read: R_i
         // occupies [114 - 12 i, 126 - 12 i), above every column j < m_w <= 6
@@ -663,7 +714,7 @@ __global__ void __launch_bounds__(kRefineThreads) elem_pass2_kernel(
             if (stored) return sl.raw(114 - 12 * i2 + 3 * a + c);
             return hq(a, 0) * sl.u(c, i2) + hq(a, 1) * sl.u(3 + c, i2) + hq(a, 2) * sl.u(6 + c, i2);
         };
-#pragma unroll
+#pragma unroll 1
         for (int q = 0; q < 10; ++q) {
             const int sa = pair_s(q), sb = pair_t(q);
             scatter_block(row_ptr, col, nnzb, fine_val, vid, sa, sb,
@@ -677,36 +728,123 @@ __global__ void __launch_bounds__(kRefineThreads) elem_pass2_kernel(
     }
 }
 
+// The Z-dependent sums of the reverse pass, accumulated one rank-one term
+// Z = p q^T at a time (p, q as 3x3, p[k][c] = p_{3k+c}):
+//   psi35 = sum z (lam Y_k[c] Y_l[d] + mu Y_k[d] Y_l[c]) and its Y-adjoint,
+//   zt_kl = sum_c z(kc, lc), R_cd = sum_kl om_kl z(kc, ld),
+//   rho_kl = sum_cd FFt_cd z(kc, ld).
+struct ZAcc {
+    double psi;
+    double Yb[3][3], zt[3][3], R[3][3], rho[3][3];
+};
+
+__device__ __forceinline__ void zacc_init(ZAcc &a)
+{
+    a.psi = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) a.Yb[i][j] = a.zt[i][j] = a.R[i][j] = a.rho[i][j] = 0.0;
+}
+
+// The element invariants the Z sums read: Y and the symmetric om and FFt,
+// from the element's registers ...
+struct ZGeomRegs {
+    const Tet &t;
+    __device__ __forceinline__ double Y(int k, int c) const { return t.Y[k][c]; }
+    __device__ __forceinline__ double om(int k, int l) const { return t.om[k][l]; }
+    __device__ __forceinline__ double FFt(int c, int d) const { return t.FFt[c][d]; }
+};
+
+// ... or with om and FFt parked in shared-memory slots (upper triangles at
+// slot base + sym3(i, j) and base + 6 + sym3(i, j)), Y in registers.
+__host__ __device__ constexpr int sym3(int i, int j) { return i <= j ? (i == 0 ? j : i == 1 ? 2 + j : 5) : sym3(j, i); }
+
+struct ZGeomShared {
+    double Yr[3][3];
+    const Slots &sl;
+    int base;
+    __device__ __forceinline__ double Y(int k, int c) const { return Yr[k][c]; }
+    __device__ __forceinline__ double om(int k, int l) const { return sl.raw(base + sym3(k, l)); }
+    __device__ __forceinline__ double FFt(int c, int d) const { return sl.raw(base + 6 + sym3(c, d)); }
+};
+
+template <class ZG>
+__device__ __forceinline__ void zacc_rank1(const ZG &t, double mu, double lam, const double P[3][3],
+                                           const double Q[3][3], ZAcc &a)
+{
+    // phases ordered so that few temporaries are live at once
+    double pa = 0.0, qb = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            pa += P[k][c] * t.Y(k, c);
+            qb += Q[k][c] * t.Y(k, c);
+        }
+    a.psi += lam * pa * qb;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) a.Yb[k][c] += lam * (qb * P[k][c] + pa * Q[k][c]);
+    // gam_kl = p_k . Y_l and del_lk = q_l . Y_k: psi_mu = mu sum gam_kl del_lk,
+    // Yb_k += mu sum_l gam_kl q_l, Yb_l += mu sum_k del_lk p_k
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+            const double gam = P[k][0] * t.Y(l, 0) + P[k][1] * t.Y(l, 1) + P[k][2] * t.Y(l, 2);
+            const double del = Q[l][0] * t.Y(k, 0) + Q[l][1] * t.Y(k, 1) + Q[l][2] * t.Y(k, 2);
+            a.psi += mu * gam * del;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                a.Yb[k][c] += mu * gam * Q[l][c];
+                a.Yb[l][c] += mu * del * P[k][c];
+            }
+        }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) a.zt[i][j] += P[i][0] * Q[j][0] + P[i][1] * Q[j][1] + P[i][2] * Q[j][2];
+    // R_cd += sum_k p_k[c] (om Q)_k[d], one column d at a time
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        double oq[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) oq[k] = t.om(k, 0) * Q[0][d] + t.om(k, 1) * Q[1][d] + t.om(k, 2) * Q[2][d];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) a.R[c][d] += P[0][c] * oq[0] + P[1][c] * oq[1] + P[2][c] * oq[2];
+    }
+    // rho_kl += p_k . (FFt q_l), one l at a time
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+        double fq[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) fq[c] = t.FFt(c, 0) * Q[l][0] + t.FFt(c, 1) * Q[l][1] + t.FFt(c, 2) * Q[l][2];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) a.rho[k][l] += P[k][0] * fq[0] + P[k][1] * fq[1] + P[k][2] * fq[2];
+    }
+}
+
 // Reverse-mode derivative of psi = <P, Lam> + <Z, Mhat> with respect to the
-// rest positions (Mhat = M / V; Z given entrywise by z(r, q), r = 3k+c).
+// rest positions (Mhat = M / V; Z enters through its accumulated sums).
 // Returns psi and adds dphi/dX (phi = V psi) to Xb.
-template <class ZF>
 __device__ __forceinline__ double reverse_phi(const Tet &t, double mu, double lam, const double lh[3][3],
-                                              bool with_lambda, ZF z, double Xb[4][3])
+                                              bool with_lambda, const ZAcc &za, double Xb[4][3])
 {
     double Fb[3][3], whb[3][3], Yb[3][3];
     double zt[3][3], R[3][3], rho[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) Fb[i][j] = whb[i][j] = Yb[i][j] = zt[i][j] = R[i][j] = rho[i][j] = 0.0;
-    double psi = 0.0;
-    // Z terms: psi35 = sum z (lam Y_k[c] Y_l[d] + mu Y_k[d] Y_l[c]); traces, R, rho
-#pragma unroll
-    for (int r = 0; r < 9; ++r)
-#pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            const int k = r / 3, c = r % 3, l = q / 3, d = q % 3;
-            const double zz = z(r, q);
-            psi += zz * (lam * t.Y[k][c] * t.Y[l][d] + mu * t.Y[k][d] * t.Y[l][c]);
-            Yb[k][c] += lam * zz * t.Y[l][d];
-            Yb[l][d] += lam * zz * t.Y[k][c];
-            Yb[k][d] += mu * zz * t.Y[l][c];
-            Yb[l][c] += mu * zz * t.Y[k][d];
-            if (c == d) zt[k][l] += zz;
-            R[c][d] += t.om[k][l] * zz;
-            rho[k][l] += t.FFt[c][d] * zz;
+        for (int j = 0; j < 3; ++j) {
+            Fb[i][j] = whb[i][j] = 0.0;
+            Yb[i][j] = za.Yb[i][j];
+            zt[i][j] = za.zt[i][j];
+            R[i][j] = za.R[i][j];
+            rho[i][j] = za.rho[i][j];
         }
+    double psi = za.psi;
     // psi2 = <S, T>, T = sum_kl zt_kl wh_k wh_l^T; psi4 = mu <FFt, R>
     double T[3][3];
 #pragma unroll
@@ -865,7 +1003,7 @@ __global__ void __launch_bounds__(128) vjp_pass1_kernel(int32_t n, int64_t nt, c
                                                         const double *__restrict__ E, double nu,
                                                         const double *__restrict__ lam_f, const double *__restrict__ dx,
                                                         double *__restrict__ dL_dE, double *dL_dX,
-                                                        int32_t *hdr, uint8_t *mcode, uint32_t *status)
+                                                        int32_t *hdr, uint8_t *mcode, EigStore es, uint32_t *status)
 {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nt; e += (int64_t)gridDim.x * blockDim.x) {
         int vid[4];
@@ -883,8 +1021,10 @@ __global__ void __launch_bounds__(128) vjp_pass1_kernel(int32_t n, int64_t nt, c
             Tet t;
             tet_eval(X, x, mu, lam, t);
             double Xb[4][3] = {};
-            const double psi = reverse_phi(t, mu, lam, lh, true,
-                                           [&](int r, int q) { return lh[r / 3][r % 3] * dh[q / 3][q % 3]; }, Xb);
+            ZAcc za;
+            zacc_init(za);
+            zacc_rank1(ZGeomRegs{t}, mu, lam, lh, dh, za);   // Z = lh dh^T (D = 1)
+            const double psi = reverse_phi(t, mu, lam, lh, true, za, Xb);
             dL_dE[e] = -t.V * psi / Ee;
 #pragma unroll
             for (int a = 0; a < 4; ++a)
@@ -894,6 +1034,7 @@ __global__ void __launch_bounds__(128) vjp_pass1_kernel(int32_t n, int64_t nt, c
             reduced_m32(t, mu, lam, A32);
             jacobi9f(A32, U32);
             flag = flagged_count(A32);
+            if (flag > 0) store_eig(es, e, A32, U32);
         }
         mcode[e] = (uint8_t)flag;
         count_flag(hdr, flag);
@@ -917,7 +1058,7 @@ __global__ void __launch_bounds__(kRefineThreads) vjp_pass2_kernel(
     int32_t n, const int32_t *__restrict__ tets, const double *__restrict__ Xr, const double *__restrict__ xc,
     const double *__restrict__ E, double nu, const double *__restrict__ lam_f, const double *__restrict__ dx,
     double *__restrict__ dL_dE, double *dL_dX, const int32_t *__restrict__ hdr,
-    const int32_t *__restrict__ list, int64_t cap)
+    const int32_t *__restrict__ list, int64_t cap, EigStore es)
 {
     __shared__ double sm[kRefineSlots * kRefineThreads];
     const Slots sl{sm, (int)threadIdx.x};
@@ -933,47 +1074,103 @@ __global__ void __launch_bounds__(kRefineThreads) vjp_pass2_kernel(
         const double Ee = E[e];
         double mu, lam;
         lame(Ee, nu, mu, lam);
-        Tet t;
-        tet_eval(X, x, mu, lam, t);
-        refine64(t, mu, lam, sl, true);
-        double L[9], av[9], bv[9];
-        for (int j = 0; j < 9; ++j) {
-            L[j] = sl.a(j, j);
-            double sa = 0.0, sb = 0.0;
+        // the eigen step and the Z sums keep only the invariants they read;
+        // the reverse pass recomputes the element (fewer live registers)
+        ZGeomShared zg{{}, sl, 108};
+        double om6[6], ff6[6];
+        {
+            Tet t;
+            tet_eval(X, x, mu, lam, t);
+            refine64(t, mu, lam, sl, true, es, e);
 #pragma unroll
-            for (int r = 0; r < 9; ++r) {
-                sa += sl.u(r, j) * lh[r / 3][r % 3];
-                sb += sl.u(r, j) * dh[r / 3][r % 3];
-            }
-            av[j] = sa;
-            bv[j] = sb;
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    zg.Yr[i][j] = t.Y[i][j];
+                    if (i <= j) {
+                        om6[sym3(i, j)] = t.om[i][j];
+                        ff6[sym3(i, j)] = t.FFt[i][j];
+                    }
+                }
         }
-        // Z = U C U^T with C = (D - 1) o (a b^T), nonzero only where an
-        // eigenvalue is <= 0
-        double Cz[9][9], Zl[9][9];
-#pragma unroll
-        for (int i2 = 0; i2 < 9; ++i2)
-#pragma unroll
-            for (int j = 0; j < 9; ++j) Cz[i2][j] = dd_minus_one(L[i2], L[j]) * av[i2] * bv[j];
-        for (int r = 0; r < 9; ++r) {
-            double tr[9];
+        // eigenvalues (A's diagonal), a = U^T lh and b = U^T dh, then into
+        // slots 81..107 and om, FFt into 108..119 once every diagonal entry of
+        // A has been read (A is not needed after that)
+        {
+            double L[9], av[9], bv[9];
 #pragma unroll
             for (int j = 0; j < 9; ++j) {
-                double acc = 0.0;
+                L[j] = sl.a(j, j);
+                double sa = 0.0, sb = 0.0;
 #pragma unroll
-                for (int i2 = 0; i2 < 9; ++i2) acc += sl.u(r, i2) * Cz[i2][j];
-                tr[j] = acc;
+                for (int r = 0; r < 9; ++r) {
+                    sa += sl.u(r, j) * lh[r / 3][r % 3];
+                    sb += sl.u(r, j) * dh[r / 3][r % 3];
+                }
+                av[j] = sa;
+                bv[j] = sb;
             }
 #pragma unroll
-            for (int q = 0; q < 9; ++q) {
-                double acc = 0.0;
+            for (int j = 0; j < 9; ++j) {
+                sl.raw(81 + j) = L[j];
+                sl.raw(90 + j) = av[j];
+                sl.raw(99 + j) = bv[j];
+            }
 #pragma unroll
-                for (int j = 0; j < 9; ++j) acc += tr[j] * sl.u(q, j);
-                Zl[r][q] = acc;
+            for (int k = 0; k < 6; ++k) {
+                sl.raw(108 + k) = om6[k];
+                sl.raw(114 + k) = ff6[k];
             }
         }
+        // Z = U C U^T with C = (D - 1) o (a b^T), nonzero only in the rows
+        // and columns of the eigenvalues <= 0 (set N): Z is the sum over
+        // i in N of u_i v_i^T + w_i u_i^T, v_i = sum_j C_ij u_j and
+        // w_i = sum_{k not in N} C_ki u_k
+        ZAcc za;
+        zacc_init(za);
+#pragma unroll 1
+        for (int i2 = 0; i2 < 9; ++i2) {
+            const double li = sl.raw(81 + i2);
+            if (li > 0.0) continue;
+            const double ai = sl.raw(90 + i2), bi = sl.raw(99 + i2);
+            double P[3][3], Q[3][3];
+#pragma unroll
+            for (int r = 0; r < 9; ++r) {
+                P[r / 3][r % 3] = sl.u(r, i2);
+                Q[r / 3][r % 3] = 0.0;
+            }
+#pragma unroll 1
+            for (int j = 0; j < 9; ++j) {
+                const double cj = ai * dd_minus_one(li, sl.raw(81 + j)) * sl.raw(99 + j);
+#pragma unroll
+                for (int r = 0; r < 9; ++r) Q[r / 3][r % 3] += cj * sl.u(r, j);
+            }
+            zacc_rank1(zg, mu, lam, P, Q, za);
+            double W[3][3];
+#pragma unroll
+            for (int r = 0; r < 9; ++r) W[r / 3][r % 3] = 0.0;
+#pragma unroll 1
+            for (int k = 0; k < 9; ++k) {
+                const double lk = sl.raw(81 + k);
+                const double ck = lk > 0.0 ? dd_minus_one(lk, li) * sl.raw(90 + k) * bi : 0.0;
+#pragma unroll
+                for (int r = 0; r < 9; ++r) W[r / 3][r % 3] += ck * sl.u(r, k);
+            }
+            zacc_rank1(zg, mu, lam, W, P, za);
+        }
+        // the element again, from fresh loads (so that X and x need not stay
+        // live through the Z sums)
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                X[a][c] = ld_fresh(Xr + 3 * (int64_t)vid[a] + c);
+                x[a][c] = ld_fresh(xc + 3 * (int64_t)vid[a] + c);
+            }
+        Tet t;
+        tet_eval(X, x, mu, lam, t);
         double Xb[4][3] = {};
-        const double psi = reverse_phi(t, mu, lam, lh, false, [&](int r, int q) { return Zl[r][q]; }, Xb);
+        const double psi = reverse_phi(t, mu, lam, lh, false, za, Xb);
         dL_dE[e] -= t.V * psi / Ee;
 #pragma unroll
         for (int a = 0; a < 4; ++a)
@@ -1105,7 +1302,11 @@ __global__ void strain_tag_kernel(int32_t n, int64_t nt, const int32_t *__restri
     }
 }
 
-int64_t workspace_words(int64_t n_tets) { return kHdr + n_tets + div_up(n_tets, 4); }
+// Workspace: kHdr header words, the list (n_tets words), the count bytes
+// (n_tets bytes), then the eigenpair records (kEigRec floats per tet) from a
+// 16-byte boundary.
+int64_t eig_offset_words(int64_t n_tets) { return div_up(kHdr + n_tets + div_up(n_tets, 4), 4) * 4; }
+int64_t workspace_words(int64_t n_tets) { return eig_offset_words(n_tets) + kEigRec * n_tets; }
 
 }  // namespace
 
@@ -1136,14 +1337,15 @@ extern "C" int agipc_fine_assemble_stvk(agipc_ctx *ctx, int32_t n_fine, int64_t 
         int32_t *list = ws + kHdr;
         uint8_t *mcode = reinterpret_cast<uint8_t *>(list + n_tets);
         if (cudaMemsetAsync(ws, 0, kHdr * sizeof(int32_t), st) != cudaSuccess) return AGIPC_ERR_CUDA;
+        const EigStore es{reinterpret_cast<float *>(ws + eig_offset_words(n_tets)), n_tets};
         elem_pass1_kernel<<<(unsigned)min64(div_up(n_tets, 128), (int64_t)ctx->num_sms * 16), 128, 0, st>>>(
-            n_fine, n_tets, tets, fine_row_ptr, fine_col, fine_nnzb, X_rest, x, E, nu, fine_val, g, ws, mcode,
+            n_fine, n_tets, tets, fine_row_ptr, fine_col, fine_nnzb, X_rest, x, E, nu, fine_val, g, ws, mcode, es,
             ctx->status);
         bucket_scatter_kernel<<<(unsigned)min64(div_up(n_tets, 256), (int64_t)ctx->num_sms * 8), 256, 0, st>>>(
             n_tets, mcode, ws, list);
         elem_pass2_kernel<<<(unsigned)min64(div_up(n_tets, kRefineThreads), (int64_t)ctx->num_sms * 7),
                             kRefineThreads, 0, st>>>(n_fine, tets, fine_row_ptr, fine_col, fine_nnzb, X_rest, x, E,
-                                                     nu, fine_val, ws, list, n_tets, ctx->status);
+                                                     nu, fine_val, ws, list, n_tets, es, ctx->status);
     }
     return cudaPeekAtLastError() == cudaSuccess ? AGIPC_OK : AGIPC_ERR_CUDA;
 }
@@ -1165,13 +1367,14 @@ extern "C" int agipc_stvk_vjp(agipc_ctx *ctx, int32_t n_fine, int64_t n_tets, co
         int32_t *list = ws + kHdr;
         uint8_t *mcode = reinterpret_cast<uint8_t *>(list + n_tets);
         if (cudaMemsetAsync(ws, 0, kHdr * sizeof(int32_t), st) != cudaSuccess) return AGIPC_ERR_CUDA;
+        const EigStore es{reinterpret_cast<float *>(ws + eig_offset_words(n_tets)), n_tets};
         vjp_pass1_kernel<<<(unsigned)min64(div_up(n_tets, 128), (int64_t)ctx->num_sms * 16), 128, 0, st>>>(
-            n_fine, n_tets, tets, X_rest, x, E, nu, lam, dx, dL_dE, dL_dX_rest, ws, mcode, ctx->status);
+            n_fine, n_tets, tets, X_rest, x, E, nu, lam, dx, dL_dE, dL_dX_rest, ws, mcode, es, ctx->status);
         bucket_scatter_kernel<<<(unsigned)min64(div_up(n_tets, 256), (int64_t)ctx->num_sms * 8), 256, 0, st>>>(
             n_tets, mcode, ws, list);
         vjp_pass2_kernel<<<(unsigned)min64(div_up(n_tets, kRefineThreads), (int64_t)ctx->num_sms * 7),
                            kRefineThreads, 0, st>>>(n_fine, tets, X_rest, x, E, nu, lam, dx, dL_dE, dL_dX_rest, ws,
-                                                    list, n_tets);
+                                                    list, n_tets, es);
     }
     return cudaPeekAtLastError() == cudaSuccess ? AGIPC_OK : AGIPC_ERR_CUDA;
 }
