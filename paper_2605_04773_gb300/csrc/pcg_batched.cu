@@ -61,10 +61,16 @@ struct BatchArgs {
 
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
 
+// cp.async stages of the S phase's FP32 slices: three where three buffers fit
+// next to the rest of the shared memory, else two.
+template <int K>
+__host__ __device__ constexpr int s_stages() { return K <= 5 ? 3 : 2; }
+
 template <int K>
 struct Layout {
     static constexpr int kWarp =
-        ((cmax(2 * bsl::Geom<float, K>::kBufBytes, bsl::Geom<double, K>::kBufBytes) + bsl::kJoinBytes) + 15) & ~15;
+        ((cmax(s_stages<K>() * bsl::Geom<float, K>::kBufBytes, bsl::Geom<double, K>::kBufBytes) + bsl::kJoinBytes) +
+         15) & ~15;
     static constexpr int kWarps = kPcgWarps * kWarp;
     static constexpr int kInt = 3 * (kBatchMaxInst + 1) * 4 + 4;           // irow, b0, sptr (+pad to 8)
     static constexpr int kDbl = 2 * kBatchMaxInst * 8 + kLocalTab * 2 * 8;  // alpha, beta, local table
@@ -417,7 +423,6 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_batched_kernel(BatchArgs A)
             const int64_t a0 = min64(gwarp * per, nact), a1 = min64(a0 + per, nact);
             int inst = a0 < a1 ? find_seg(s_aptr, ni, a0) : 0;
             double dsum = 0.0;
-            int nb = 0;
             auto slice_of = [&](int64_t a, int &si, int64_t &abase, int &qlo, int &cnt) {
                 while (a >= s_aptr[si + 1]) ++si;
                 const int64_t j = a - s_aptr[si];
@@ -426,29 +431,35 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_batched_kernel(BatchArgs A)
                 qlo = (int)max64(0, s_b0[si] - ab);
                 cnt = (int)min64(S, s_b0[si + 1] - ab);
             };
-            int si = inst;
-            if (a0 < a1) {
-                int64_t ab;
-                int ql, cn;
-                slice_of(a0, si, ab, ql, cn);
-                bsl::stage<float, K>(wbuf, ab, cn, A.val32, A.col, brow, lane);
+            // NS-stage pipeline: slice a + NS - 1 streams in while slice a is used
+            constexpr int NS = s_stages<K>();
+            constexpr int kFB = bsl::Geom<float, K>::kBufBytes;
+            int sp = inst;   // instance cursor of the prefetch, monotone like a
+#pragma unroll
+            for (int q = 0; q < NS - 1; ++q) {
+                if (a0 + q < a1) {
+                    int64_t ab;
+                    int ql, cn;
+                    slice_of(a0 + q, sp, ab, ql, cn);
+                    bsl::stage<float, K>(wbuf + q * kFB, ab, cn, A.val32, A.col, brow, lane);
+                }
+                cp_async_commit();
             }
-            cp_async_commit();
+            int cur = 0;     // buffer of slice a
             for (int64_t a = a0; a < a1; ++a) {
                 int64_t ab;
                 int ql, cn;
                 int sj = inst;
                 slice_of(a, sj, ab, ql, cn);
-                if (a + 1 < a1) {
+                if (a + NS - 1 < a1) {
                     int64_t ab2;
                     int ql2, cn2;
-                    int sk = sj;
-                    slice_of(a + 1, sk, ab2, ql2, cn2);
-                    bsl::stage<float, K>(wbuf + (nb ^ 1) * bsl::Geom<float, K>::kBufBytes, ab2, cn2, A.val32,
-                                         A.col, brow, lane);
+                    slice_of(a + NS - 1, sp, ab2, ql2, cn2);
+                    const int nbuf = cur + NS - 1 >= NS ? cur - 1 : cur + NS - 1;
+                    bsl::stage<float, K>(wbuf + nbuf * kFB, ab2, cn2, A.val32, A.col, brow, lane);
                 }
                 cp_async_commit();
-                cp_async_wait<1>();
+                cp_async_wait<NS - 1>();
                 __syncwarp();
                 if (sj != inst) {
                     const double t = warp_sum(dsum);
@@ -456,9 +467,8 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_batched_kernel(BatchArgs A)
                     dsum = 0.0;
                     inst = sj;
                 }
-                dsum += bsl::spmv<float, true, K>(wbuf + nb * bsl::Geom<float, K>::kBufBytes, ql, cn, u, w, rowflag,
-                                                   join, lane);
-                nb ^= 1;
+                dsum += bsl::spmv<float, true, K>(wbuf + cur * kFB, ql, cn, u, w, rowflag, join, lane);
+                cur = cur + 1 == NS ? 0 : cur + 1;
             }
             cp_async_wait<0>();
             const double t = warp_sum(dsum);

@@ -20,6 +20,7 @@ constexpr int kWarpSmem = 2 * kBufBytes + kJoinBytes;
 constexpr int kPartBytes = kPcgBlock * 3 * 8;
 constexpr int kPcgSmem = kPcgWarps * kWarpSmem + kPartBytes;
 constexpr int kMaxGridLanes = 8;               // the grid reduction handles up to 256 CTAs
+constexpr int kWalkMax = 2;                    // longer chains of whole-lane rows take the scan join
 
 
 __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src, int src_bytes)
@@ -104,6 +105,89 @@ __device__ __forceinline__ float dsel(bool c, float a, float b)
     return __int_as_float(c ? __float_as_int(a) : __float_as_int(b));
 }
 
+// Stores the rows that cross lanes of a warp slice.  Each lane passes its
+// first segment (row fr, partial fa; the lane's only one when lr < 0) and its
+// last segment (row lr, partial la).  A lane's tail row may continue into the
+// next lanes, whose head rows then carry on.  Short chains are joined by the
+// lane where the row starts, walking forward through shared memory; when
+// more than kWalkMax lanes lie wholly inside one row (the rows of large
+// aggregates), a segmented inclusive scan over the lanes (5 shuffle steps)
+// replaces the walk and the lane where a row's run of lanes ends stores it.
+template <class T>
+__device__ __forceinline__ void join_rows(int lane, int fr, T (&fa)[3], bool f_split, int lr, T (&la)[3], bool l_split,
+                                          T *w, unsigned char *join)
+{
+    const bool single = lr < 0;
+    const int tr = single ? fr : lr;
+    // every lane takes part in the shuffles and the ballot (full mask)
+    const int tr_prev = __shfl_up_sync(kFull, tr, 1);
+    const bool cont = lane > 0 && fr >= 0 && fr == tr_prev;
+    const unsigned chain = __ballot_sync(kFull, single && cont);
+    if (__popc(chain) > kWalkMax) {
+        T v[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[c] = single ? fa[c] : la[c];
+        int st = (single && cont) ? 0 : 1;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            T o[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) o[c] = __shfl_up_sync(kFull, v[c], d);
+            const int ost = __shfl_up_sync(kFull, st, d);
+            if (lane >= d && !st) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) v[c] += o[c];
+                st = ost;
+            }
+        }
+        T ci[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const T prev = __shfl_up_sync(kFull, v[c], 1);
+            ci[c] = cont ? prev : T(0);
+        }
+        const int cont_next = __shfl_down_sync(kFull, cont ? 1 : 0, 1);
+        const bool next_cont = lane < 31 && cont_next != 0;
+        if (!single && fr >= 0) {
+            T y[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) y[c] = ci[c] + fa[c];
+            store_row(w, fr, f_split, y);
+        }
+        if (tr >= 0 && !next_cont) store_row(w, tr, single ? f_split : l_split, v);
+        __syncwarp();
+        return;
+    }
+    T *s_fa = reinterpret_cast<T *>(join);
+    int32_t *s_fr = reinterpret_cast<int32_t *>(join + 32 * 24);
+    int32_t *s_single = s_fr + 32;
+    int32_t *s_last = s_fr + 64;
+    s_fr[lane] = fr;
+    s_single[lane] = single ? 1 : 0;
+    s_last[lane] = tr;
+    s_fa[3 * lane] = fa[0];
+    s_fa[3 * lane + 1] = fa[1];
+    s_fa[3 * lane + 2] = fa[2];
+    __syncwarp();
+    if (!single) {
+        for (int q = lane + 1; q < 32 && s_fr[q] == lr; ++q) {
+            la[0] += s_fa[3 * q]; la[1] += s_fa[3 * q + 1]; la[2] += s_fa[3 * q + 2];
+            if (!s_single[q]) break;
+        }
+        store_row(w, lr, l_split, la);
+    }
+    if (fr >= 0 && (lane == 0 || s_last[lane - 1] != fr)) {
+        if (single) {
+            for (int q = lane + 1; q < 32 && s_fr[q] == fr; ++q) {
+                fa[0] += s_fa[3 * q]; fa[1] += s_fa[3 * q + 1]; fa[2] += s_fa[3 * q + 2];
+                if (!s_single[q]) break;
+            }
+        }
+        store_row(w, fr, f_split, fa);
+    }
+    __syncwarp();
+}
+
 // w = A u over one slice held in `buf` (rows inside the slice) or += (rows
 // cut by its ends); with kDelta, adds this lane's share of delta = u . A u
 // (accumulated in T over the lane's row segments) to dpart.  T is the type
@@ -112,9 +196,12 @@ __device__ __forceinline__ float dsel(bool c, float a, float b)
 // Per lane the 5 blocks are folded left to right into one running row
 // accumulator (reset at a row change by a select, so the FP64 work is
 // exactly 9 FMAs per block with no divergence); a row segment's total is the
-// accumulator at the segment's last block.  delta takes u_row . total at
-// each segment end.  Segments that cross lanes are joined by the lane where
-// the row starts, which walks forward over the lanes that continue it.
+// accumulator at the segment's last block.  delta is linear in w, so each
+// lane adds u_row . (its own part of the row) once per segment: for its
+// first and last segments after the fold (6 FMAs), for the rare rows wholly
+// inside the lane where they are stored.  Segments that cross lanes are
+// joined by the lane where the row starts, which walks forward over the
+// lanes that continue it.
 template <class T, bool kDelta>
 __device__ __forceinline__ void slice_spmv(const unsigned char *buf, int cnt, const T *u, T *w,
                                            const uint8_t *rowflag, unsigned char *join, int lane, double &dpart)
@@ -152,6 +239,7 @@ __device__ __forceinline__ void slice_spmv(const unsigned char *buf, int cnt, co
     // running accumulator; segment bookkeeping by selects
     T acc[3] = {T(0), T(0), T(0)};
     T fa[3] = {T(0), T(0), T(0)}, la[3] = {T(0), T(0), T(0)};
+    T fu[3] = {T(0), T(0), T(0)}, lu[3] = {T(0), T(0), T(0)};
     T dloc = T(0);
     int fr = -1, lr = -1;
     bool f_split = false, l_split = false, s_cur = false, first_open = true;
@@ -174,53 +262,30 @@ __device__ __forceinline__ void slice_spmv(const unsigned char *buf, int cnt, co
             acc[c] = fma(B[3 * c + 2], xv[j][2], fma(B[3 * c + 1], xv[j][1], fma(B[3 * c], xv[j][0], acc[c])));
         }
         s_cur = start ? split[j] : s_cur;
-        // delta: u_row . segment total at every segment end (zero elsewhere)
-        if (kDelta)
-            dloc = fma(dsel(end, cu[0], T(0)), acc[0], fma(dsel(end, cu[1], T(0)), acc[1], fma(dsel(end, cu[2], T(0)), acc[2], dloc)));
         if (end) {
             const bool last = j == kK - 1 || rows_[j + 1] < 0;
             if (first_open) {                       // the lane's first segment: joined below
                 fr = rows_[j]; f_split = s_cur;
                 fa[0] = acc[0]; fa[1] = acc[1]; fa[2] = acc[2];
+                fu[0] = cu[0]; fu[1] = cu[1]; fu[2] = cu[2];
                 first_open = false;
             } else if (last) {                      // the lane's last segment: joined below
                 lr = rows_[j]; l_split = s_cur;
                 la[0] = acc[0]; la[1] = acc[1]; la[2] = acc[2];
+                lu[0] = cu[0]; lu[1] = cu[1]; lu[2] = cu[2];
             } else {                                // a row wholly inside this lane
+                if (kDelta) dloc = fma(cu[0], acc[0], fma(cu[1], acc[1], fma(cu[2], acc[2], dloc)));
                 store_row(w, rows_[j], s_cur, acc);
             }
         }
     }
-    if (kDelta) dpart += (double)dloc;
-    const bool single = lr < 0;
-    T *s_fa = reinterpret_cast<T *>(join);
-    int32_t *s_fr = reinterpret_cast<int32_t *>(join + 32 * 24);
-    int32_t *s_single = s_fr + 32;
-    int32_t *s_last = s_fr + 64;
-    s_fr[lane] = fr;
-    s_single[lane] = single ? 1 : 0;
-    s_last[lane] = single ? fr : lr;
-    s_fa[3 * lane] = fa[0];
-    s_fa[3 * lane + 1] = fa[1];
-    s_fa[3 * lane + 2] = fa[2];
-    __syncwarp();
-    if (!single) {
-        for (int q = lane + 1; q < 32 && s_fr[q] == lr; ++q) {
-            la[0] += s_fa[3 * q]; la[1] += s_fa[3 * q + 1]; la[2] += s_fa[3 * q + 2];
-            if (!s_single[q]) break;
-        }
-        store_row(w, lr, l_split, la);
+    if (kDelta) {
+        // this lane's parts of its first and last rows (zeros when absent)
+        dloc = fma(fu[0], fa[0], fma(fu[1], fa[1], fma(fu[2], fa[2], dloc)));
+        dloc = fma(lu[0], la[0], fma(lu[1], la[1], fma(lu[2], la[2], dloc)));
+        dpart += (double)dloc;
     }
-    if (fr >= 0 && (lane == 0 || s_last[lane - 1] != fr)) {
-        if (single) {
-            for (int q = lane + 1; q < 32 && s_fr[q] == fr; ++q) {
-                fa[0] += s_fa[3 * q]; fa[1] += s_fa[3 * q + 1]; fa[2] += s_fa[3 * q + 2];
-                if (!s_single[q]) break;
-            }
-        }
-        store_row(w, fr, f_split, fa);
-    }
-    __syncwarp();
+    join_rows(lane, fr, fa, f_split, lr, la, l_split, w, join);
 }
 
 }  // namespace pcgs

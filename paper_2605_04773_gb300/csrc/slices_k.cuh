@@ -44,10 +44,10 @@ __device__ __forceinline__ void stage(unsigned char *buf, int64_t abase, int cnt
 
 // w = A u over the valid positions of one staged slice (rows inside the
 // slice stored, rows cut by its ends added atomically); with kDelta returns
-// this lane's share of u . A u (accumulated in T, per row segment end).
+// this lane's share of u . A u (accumulated in T, once per row segment).
 // Same folding as pcgs::slice_spmv: one running accumulator per lane reset
 // by selects at row starts, 9 FMAs per block, segments that cross lanes
-// joined by the lane where the row starts.
+// joined by pcgs::join_rows.
 template <class T, bool kDelta, int K>
 __device__ __forceinline__ double spmv(const unsigned char *buf, int qlo, int cnt, const T *u, T *w,
                                        const uint8_t *rowflag, unsigned char *join, int lane)
@@ -85,6 +85,7 @@ __device__ __forceinline__ double spmv(const unsigned char *buf, int qlo, int cn
     }
     T acc[3] = {T(0), T(0), T(0)};
     T fa[3] = {T(0), T(0), T(0)}, la[3] = {T(0), T(0), T(0)};
+    T fu[3] = {T(0), T(0), T(0)}, lu[3] = {T(0), T(0), T(0)};
     T dloc = T(0);
     int fr = -1, lr = -1;
     bool f_split = false, l_split = false, s_cur = false, first_open = true;
@@ -107,9 +108,6 @@ __device__ __forceinline__ double spmv(const unsigned char *buf, int qlo, int cn
             acc[c] = fma(B[3 * c + 2], xv[j][2], fma(B[3 * c + 1], xv[j][1], fma(B[3 * c], xv[j][0], acc[c])));
         }
         s_cur = start ? split[j] : s_cur;
-        if (kDelta)
-            dloc = fma(dsel(end, cu[0], T(0)), acc[0],
-                       fma(dsel(end, cu[1], T(0)), acc[1], fma(dsel(end, cu[2], T(0)), acc[2], dloc)));
         if (end) {
             const bool last = j == K - 1 || rows_[j + 1] < 0;
             if (first_open) {
@@ -118,6 +116,9 @@ __device__ __forceinline__ double spmv(const unsigned char *buf, int qlo, int cn
                 fa[0] = acc[0];
                 fa[1] = acc[1];
                 fa[2] = acc[2];
+                fu[0] = cu[0];
+                fu[1] = cu[1];
+                fu[2] = cu[2];
                 first_open = false;
             } else if (last) {
                 lr = rows_[j];
@@ -125,44 +126,21 @@ __device__ __forceinline__ double spmv(const unsigned char *buf, int qlo, int cn
                 la[0] = acc[0];
                 la[1] = acc[1];
                 la[2] = acc[2];
+                lu[0] = cu[0];
+                lu[1] = cu[1];
+                lu[2] = cu[2];
             } else {
+                if (kDelta) dloc = fma(cu[0], acc[0], fma(cu[1], acc[1], fma(cu[2], acc[2], dloc)));
                 store_row(w, rows_[j], s_cur, acc);
             }
         }
     }
-    const bool single = lr < 0;
-    T *s_fa = reinterpret_cast<T *>(join);
-    int32_t *s_fr = reinterpret_cast<int32_t *>(join + 32 * 24);
-    int32_t *s_single = s_fr + 32;
-    int32_t *s_last = s_fr + 64;
-    s_fr[lane] = fr;
-    s_single[lane] = single ? 1 : 0;
-    s_last[lane] = single ? fr : lr;
-    s_fa[3 * lane] = fa[0];
-    s_fa[3 * lane + 1] = fa[1];
-    s_fa[3 * lane + 2] = fa[2];
-    __syncwarp();
-    if (!single) {
-        for (int q = lane + 1; q < 32 && s_fr[q] == lr; ++q) {
-            la[0] += s_fa[3 * q];
-            la[1] += s_fa[3 * q + 1];
-            la[2] += s_fa[3 * q + 2];
-            if (!s_single[q]) break;
-        }
-        store_row(w, lr, l_split, la);
+    if (kDelta) {
+        // delta is linear in w: this lane's parts of its first and last rows
+        dloc = fma(fu[0], fa[0], fma(fu[1], fa[1], fma(fu[2], fa[2], dloc)));
+        dloc = fma(lu[0], la[0], fma(lu[1], la[1], fma(lu[2], la[2], dloc)));
     }
-    if (fr >= 0 && (lane == 0 || s_last[lane - 1] != fr)) {
-        if (single) {
-            for (int q = lane + 1; q < 32 && s_fr[q] == fr; ++q) {
-                fa[0] += s_fa[3 * q];
-                fa[1] += s_fa[3 * q + 1];
-                fa[2] += s_fa[3 * q + 2];
-                if (!s_single[q]) break;
-            }
-        }
-        store_row(w, fr, f_split, fa);
-    }
-    __syncwarp();
+    pcgs::join_rows(lane, fr, fa, f_split, lr, la, l_split, w, join);
     return (double)dloc;
 }
 
