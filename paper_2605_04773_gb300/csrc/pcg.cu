@@ -139,7 +139,10 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_kernel(PcgArgs A)
     uint8_t *rowflag = A.S.rowflag;
     double *partials = A.S.partials;
     unsigned *count = A.S.bar;
-    const int pstride = A.S.max_grid * 4;
+    // partial sums: scalar s of CTA k at [s * mg + k] (scalar-major, so a
+    // warp reducing one scalar reads consecutive words)
+    const int mg = A.S.max_grid;
+    const int pstride = mg * 4;
     unsigned epoch = 0;
     unsigned char *wbuf = smem + (size_t)wib * kWarpSmem;
     unsigned char *join = wbuf + 2 * kBufBytes;
@@ -223,9 +226,9 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_kernel(PcgArgs A)
         double v[3] = {gpart, rpart, bpart};
         cta_sum<3>(v, s_part, s_tot);
         if (threadIdx.x == 0) {
-            partials[blockIdx.x * 4 + 0] = v[0];
-            partials[blockIdx.x * 4 + 1] = v[1];
-            partials[blockIdx.x * 4 + 3] = v[2];
+            partials[0 * mg + blockIdx.x] = v[0];
+            partials[1 * mg + blockIdx.x] = v[1];
+            partials[3 * mg + blockIdx.x] = v[2];
         }
     }
     ok = grid_sync(count, nblocks, epoch, A.status) && ok;
@@ -285,7 +288,7 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_kernel(PcgArgs A)
         {
             double v[1] = {dpart};
             cta_sum<1>(v, s_part, s_tot);
-            if (threadIdx.x == 0) part[blockIdx.x * 4 + 2] = v[0];
+            if (threadIdx.x == 0) part[2 * mg + blockIdx.x] = v[0];
         }
         if (!grid_sync(count, nblocks, epoch, A.status)) { ok = false; break; }
         if (has_row) {
@@ -302,7 +305,7 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_kernel(PcgArgs A)
 #pragma unroll
             for (int q = 0; q < kMaxGridLanes; ++q) {
                 const unsigned k = lane + 32 * q;
-                pv[q] = k < nblocks ? __ldcg(part + k * 4 + wib) : 0.0;
+                pv[q] = k < nblocks ? __ldcg(part + wib * mg + k) : 0.0;
             }
 #pragma unroll
             for (int h = kMaxGridLanes / 2; h > 0; h >>= 1)
@@ -380,8 +383,8 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_kernel(PcgArgs A)
             double v[2] = {gpart, rpart};
             cta_sum<2>(v, s_part, s_tot);
             if (threadIdx.x == 0) {
-                npart[blockIdx.x * 4 + 0] = v[0];
-                npart[blockIdx.x * 4 + 1] = v[1];
+                npart[0 * mg + blockIdx.x] = v[0];
+                npart[1 * mg + blockIdx.x] = v[1];
             }
         }
         ++it;
