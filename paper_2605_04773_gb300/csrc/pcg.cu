@@ -15,14 +15,14 @@
 // whatever its active mask (65-cycle dependent latency), so the kernel
 // counts FP64 warp instructions: a 3x3 block costs 9 FMAs and everything
 // else per block, per row and per reduction is kept small next to that.
-//   S phase (w = A u): the blocks are cut into slices of 160 (32 lanes x 5
+//   S phase (w = A u): the blocks are cut into slices of 128 (32 lanes x 4
 //     consecutive blocks); slices go round-robin to warps spread over all
 //     CTAs.  Each warp owns two shared-memory buffers for its slices, filled
 //     by cp.async copies: when the matrix fits in shared memory (at most one
 //     slice per warp) the slice is loaded once and stays resident for the
 //     whole solve; otherwise the next slice (also the first slice of the next
 //     iteration) streams in while the current one is multiplied.  Each lane
-//     accumulates its 5 blocks in registers, one accumulator per row segment;
+//     accumulates its 4 blocks in registers, one accumulator per row segment;
 //     segments that cross lanes are joined by the lane where the row starts.
 //     Column gathers of u, u of the lane's rows (for delta) and the rows'
 //     split flags are all issued together, so emitting a row never waits on a

@@ -9,7 +9,7 @@
 // on GB300 are ~56x faster than the FP64 ones.
 //
 // Same structure as the FP64 kernel (pcg.cu): one persistent cooperative
-// launch, Chronopoulos-Gear recurrence, FP32 slices of 160 blocks staged by
+// launch, Chronopoulos-Gear recurrence, FP32 slices of 128 blocks staged by
 // cp.async and resident in shared memory when they fit.  A refinement
 // iteration adds an FP64 slice SpMV of x (staged in the warp's free buffer)
 // and one grid barrier.
