@@ -61,22 +61,23 @@ struct BatchArgs {
 
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
 
-// cp.async stages of the S phase's FP32 slices: three where three buffers fit
-// next to the rest of the shared memory, else two.
+// cp.async stages of the S phase's FP32 slices: three for the narrow tiles,
+// two for the wide ones.  More stages fit, but shared memory then crowds out
+// the L1 that the u gathers hit (4 stages at 4 blocks a lane and 3 at 6 were
+// 9 % and 17 % slower on the 256-instance batch).
 template <int K>
 __host__ __device__ constexpr int s_stages() { return K <= 5 ? 3 : 2; }
 
 template <int K>
 struct Layout {
     static constexpr int kWarp =
-        ((cmax(s_stages<K>() * bsl::Geom<float, K>::kBufBytes, bsl::Geom<double, K>::kBufBytes) + bsl::kJoinBytes) +
-         15) & ~15;
+        (cmax(s_stages<K>() * bsl::Geom<float, K>::kBufBytes, bsl::Geom<double, K>::kBufBytes) + 15) & ~15;
     static constexpr int kWarps = kPcgWarps * kWarp;
     static constexpr int kInt = 3 * (kBatchMaxInst + 1) * 4 + 4;           // irow, b0, sptr (+pad to 8)
     static constexpr int kDbl = 2 * kBatchMaxInst * 8 + kLocalTab * 2 * 8;  // alpha, beta, local table
     static constexpr int kScan = (kBatchMaxInst + 1) * 4 * 4;               // active/refine slice and row prefixes
     static constexpr int kByte = 2 * kBatchMaxInst;                         // dec, ref
-    static constexpr int kTotal = kWarps + kPartBytes + kInt + kDbl + kScan + kByte;
+    static constexpr int kTotal = kWarps + kInt + kDbl + kScan + kByte;
 };
 
 __device__ __forceinline__ void precond32(const float *D, const double r[3], float u[3])
@@ -172,19 +173,18 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_batched_kernel(BatchArgs A)
     const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
 
     unsigned char *wbuf = smem + (size_t)wib * L::kWarp;
-    unsigned char *join = wbuf + L::kWarp - bsl::kJoinBytes;
-    double *s_part = reinterpret_cast<double *>(smem + L::kWarps);
-    int32_t *s_irow = reinterpret_cast<int32_t *>(smem + L::kWarps + kPartBytes);
+    unsigned char *join = nullptr;   // the batched slices join rows by shuffles only
+    int32_t *s_irow = reinterpret_cast<int32_t *>(smem + L::kWarps);
     int32_t *s_b0 = s_irow + (kBatchMaxInst + 1);
     int32_t *s_sptr = s_b0 + (kBatchMaxInst + 1);
-    double *s_alpha = reinterpret_cast<double *>(smem + L::kWarps + kPartBytes + L::kInt);
+    double *s_alpha = reinterpret_cast<double *>(smem + L::kWarps + L::kInt);
     double *s_beta = s_alpha + kBatchMaxInst;
     double *s_tab = s_beta + kBatchMaxInst;
-    int32_t *s_aptr = reinterpret_cast<int32_t *>(smem + L::kWarps + kPartBytes + L::kInt + L::kDbl);
+    int32_t *s_aptr = reinterpret_cast<int32_t *>(smem + L::kWarps + L::kInt + L::kDbl);
     int32_t *s_rptr = s_aptr + (kBatchMaxInst + 1);
     int32_t *s_arow = s_rptr + (kBatchMaxInst + 1);
     int32_t *s_rrow = s_arow + (kBatchMaxInst + 1);
-    int8_t *s_dec = reinterpret_cast<int8_t *>(smem + L::kWarps + kPartBytes + L::kInt + L::kDbl + L::kScan);
+    int8_t *s_dec = reinterpret_cast<int8_t *>(smem + L::kWarps + L::kInt + L::kDbl + L::kScan);
     int8_t *s_ref = s_dec + kBatchMaxInst;
 
     const int ni = A.n_inst;

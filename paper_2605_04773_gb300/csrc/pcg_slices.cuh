@@ -115,7 +115,8 @@ __device__ __forceinline__ float dsel(bool c, float a, float b)
 // more than kWalkMax lanes lie wholly inside one row (the rows of large
 // aggregates), a segmented inclusive scan over the lanes (5 shuffle steps)
 // replaces the walk and the lane where a row's run of lanes ends stores it.
-template <class T>
+// kScanOnly always takes the scan (no shared memory; `join` unused).
+template <class T, bool kScanOnly = false>
 __device__ __forceinline__ void join_rows(int lane, int fr, T (&fa)[3], bool f_split, int lr, T (&la)[3], bool l_split,
                                           T *w, unsigned char *join)
 {
@@ -125,7 +126,7 @@ __device__ __forceinline__ void join_rows(int lane, int fr, T (&fa)[3], bool f_s
     const int tr_prev = __shfl_up_sync(kFull, tr, 1);
     const bool cont = lane > 0 && fr >= 0 && fr == tr_prev;
     const unsigned chain = __ballot_sync(kFull, single && cont);
-    if (__popc(chain) > kWalkMax) {
+    if (kScanOnly || __popc(chain) > kWalkMax) {
         T v[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) v[c] = single ? fa[c] : la[c];

@@ -47,7 +47,8 @@ __device__ __forceinline__ void stage(unsigned char *buf, int64_t abase, int cnt
 // this lane's share of u . A u (accumulated in T, once per row segment).
 // Same folding as pcgs::slice_spmv: one running accumulator per lane reset
 // by selects at row starts, 9 FMAs per block, segments that cross lanes
-// joined by pcgs::join_rows.
+// joined by pcgs::join_rows with the shuffle scan only (no shared memory,
+// so the warp's buffers can take a further pipeline stage; `join` unused).
 template <class T, bool kDelta, int K>
 __device__ __forceinline__ double spmv(const unsigned char *buf, int qlo, int cnt, const T *u, T *w,
                                        const uint8_t *rowflag, unsigned char *join, int lane)
@@ -140,7 +141,7 @@ __device__ __forceinline__ double spmv(const unsigned char *buf, int qlo, int cn
         dloc = fma(fu[0], fa[0], fma(fu[1], fa[1], fma(fu[2], fa[2], dloc)));
         dloc = fma(lu[0], la[0], fma(lu[1], la[1], fma(lu[2], la[2], dloc)));
     }
-    pcgs::join_rows(lane, fr, fa, f_split, lr, la, l_split, w, join);
+    pcgs::join_rows<T, true>(lane, fr, fa, f_split, lr, la, l_split, w, join);
     return (double)dloc;
 }
 
