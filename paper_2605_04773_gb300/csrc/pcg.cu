@@ -29,7 +29,9 @@
 //     load.  A row inside one slice is stored; a row cut by a slice boundary
 //     is added with FP64 atomics (w of such rows is zeroed in the P phase).
 //   P phase: rows are split evenly over the CTAs; each thread does the
-//     row-local updates, the 3x3 preconditioner and its share of gamma, rho.
+//     row-local updates, the 3x3 preconditioner and its share of gamma, rho;
+//     the CTA's sums of those shares are formed during the next S phase by
+//     the CTA's last warp (the one with the fewest slices).
 //   CTA sums go through shared memory, one warp per summed value; CTA
 //     partials go to per-CTA slots and every CTA reduces all slots in the
 //     same order (again one warp per value), so the scalars are bitwise
@@ -103,6 +105,7 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_kernel(PcgArgs A)
     __shared__ double s_scal[2];
     __shared__ double s_tot[4];
     __shared__ double s_grid[4];
+    __shared__ double s_gr[2 * kPcgBlock];   // the P phase's per-thread gamma, rho shares
     __shared__ int s_dec;
 
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -268,6 +271,30 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_kernel(PcgArgs A)
             slice_spmv<double, true>(wbuf + nb * kBufBytes, cnt, u, w, rowflag, join, lane, dpart);
             if (!resident) nb ^= 1;
         }
+        if (it > 0 && wib == kPcgWarps - 1) {
+            // the previous P phase's gamma and rho shares, summed over the CTA
+            // (fixed order) by the last warp, which holds the fewest slices, so
+            // the sum overlaps the other warps' SpMV instead of delaying the
+            // barrier after the P phase
+            double t0[kPcgWarps], t1[kPcgWarps];
+#pragma unroll
+            for (int q = 0; q < kPcgWarps; ++q) {
+                t0[q] = s_gr[2 * (lane + 32 * q)];
+                t1[q] = s_gr[2 * (lane + 32 * q) + 1];
+            }
+#pragma unroll
+            for (int h = kPcgWarps / 2; h > 0; h >>= 1)
+#pragma unroll
+                for (int q = 0; q < h; ++q) {
+                    t0[q] += t0[q + h];
+                    t1[q] += t1[q + h];
+                }
+            const double g0 = warp_sum(t0[0]), g1 = warp_sum(t1[0]);
+            if (lane == 0) {
+                part[0 * mg + blockIdx.x] = g0;
+                part[1 * mg + blockIdx.x] = g1;
+            }
+        }
         // one row per thread: fetch the row's own state now, so that only w
         // (written by other CTAs) is read after the barrier
         const int64_t my_row = row0 + threadIdx.x;
@@ -355,8 +382,8 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_kernel(PcgArgs A)
         if (decision == 1) { converged = true; break; }
         if (decision == 2) break;
 
-        // ---- P phase: row-local updates, preconditioner, next partials
-        double *npart = partials + (par ^ 1) * pstride;
+        // ---- P phase: row-local updates, preconditioner, gamma and rho shares
+        // (summed over the CTA during the next S phase)
         gpart = 0.0;
         rpart = 0.0;
         if (one_row) {
@@ -379,14 +406,8 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_kernel(PcgArgs A)
                 row_update(i, uu, ww, pp, ss, rr, xx, D, alpha, beta, p, s, r, x, u, w, rowflag[i] != 0, gpart, rpart);
             }
         }
-        {
-            double v[2] = {gpart, rpart};
-            cta_sum<2>(v, s_part, s_tot);
-            if (threadIdx.x == 0) {
-                npart[0 * mg + blockIdx.x] = v[0];
-                npart[1 * mg + blockIdx.x] = v[1];
-            }
-        }
+        s_gr[2 * threadIdx.x] = gpart;
+        s_gr[2 * threadIdx.x + 1] = rpart;
         ++it;
         if (!grid_sync(count, nblocks, epoch, A.status)) { ok = false; break; }
     }

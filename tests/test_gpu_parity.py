@@ -158,6 +158,25 @@ def test_unit_cube_full_path_parity():
     assert np.linalg.norm(got["dx"] - ref["dx"]) <= 1e-6 * np.linalg.norm(ref["dx"])
 
 
+@pytest.mark.parametrize("cells", [8, 14])
+def test_long_coarse_rows(cells):
+    """One large interior aggregate wrapped in protected boundary vertices:
+    its coarse row holds hundreds of blocks (spanning many warp lanes and
+    several slices), next to many short rows, so the SpMV joins rows both
+    ways (shuffle scan for long chains, the walk for short ones)."""
+    sc = scenes.tiny_box(seed=77 + cells, nx=cells, ny=cells, nz=cells, n_pairs=4, frac=0.5)
+    X = sc.meta["X_rest"]
+    lo, hi = X.min(0), X.max(0)
+    cell = (hi[0] - lo[0]) / cells
+    interior = np.all((X > lo + 0.5 * cell) & (X < hi - 0.5 * cell), axis=1)
+    tags = (interior[sc.edges[:, 0]] & interior[sc.edges[:, 1]]).astype(np.uint8)
+    rc, got = _run(sc, tags, tol=1e-10)
+    assert rc == agipc.OK
+    crp, cci, cval, gc = _check_coarse(sc, got, tags)
+    assert np.diff(crp).max() > 256   # longer than two 128-block slices
+    _check_solve(got, crp, cci, cval, gc, 1e-10)
+
+
 def test_single_supernode_and_all_protected():
     sc = scenes.unit_cube(seed=1003)
     rc, got = _run(sc, np.ones(sc.n_edges, np.uint8), tol=1e-12)
