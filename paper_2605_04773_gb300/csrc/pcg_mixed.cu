@@ -56,6 +56,7 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_mixed_kernel(MixedArgs A)
     __shared__ double s_scal[2];
     __shared__ double s_tot[4];
     __shared__ double s_grid[3];
+    __shared__ double s_gr[2 * kPcgBlock];   // the P phase's per-thread gamma, rho shares
     __shared__ int s_dec;
     __shared__ bool s_ref;
 
@@ -159,6 +160,7 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_mixed_kernel(MixedArgs A)
     bool tight = false, last_verify = false, restart = false;
     int32_t it = 0;
     bool converged = false;
+    bool pending = false;   // gamma, rho shares of a P phase wait in s_gr
     while (ok) {
         const int par = it & 1;
         double *part = partials + par * pstride;
@@ -177,6 +179,28 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_mixed_kernel(MixedArgs A)
             const int cnt = (int)min64(kSlice, nnz - sl * kSlice);
             slice_spmv<float, true>(wbuf + nb * kBufBytes, cnt, u, w, rowflag, join, lane, dpart);
             if (!resident) nb ^= 1;
+        }
+        if (pending && wib == kPcgWarps - 1) {
+            // the previous P phase's gamma and rho shares, summed over the CTA
+            // (fixed order) by the last warp while the others multiply
+            double t0[kPcgWarps], t1[kPcgWarps];
+#pragma unroll
+            for (int q = 0; q < kPcgWarps; ++q) {
+                t0[q] = s_gr[2 * (lane + 32 * q)];
+                t1[q] = s_gr[2 * (lane + 32 * q) + 1];
+            }
+#pragma unroll
+            for (int h = kPcgWarps / 2; h > 0; h >>= 1)
+#pragma unroll
+                for (int q = 0; q < h; ++q) {
+                    t0[q] += t0[q + h];
+                    t1[q] += t1[q + h];
+                }
+            const double g0 = warp_sum(t0[0]), g1 = warp_sum(t1[0]);
+            if (lane == 0) {
+                part[0 * mg + blockIdx.x] = g0;
+                part[1 * mg + blockIdx.x] = g1;
+            }
         }
         {
             double v[1] = {dpart};
@@ -262,8 +286,9 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_mixed_kernel(MixedArgs A)
         const float beta32 = (float)beta;
         // ---- P phase.  The next reduction reads the slot of parity (it + 1);
         // a verify step does not advance it, so its partials go to slot `par`
-        // (already read by every CTA two barriers ago).
-        double *npart = partials + (verify ? par : par ^ 1) * pstride;
+        // (already read by every CTA two barriers ago).  The CTA's sums of
+        // the gamma, rho shares are formed in the next S phase, which writes
+        // them to that slot.
         gpart = 0.0;
         rpart = 0.0;
         for (int64_t i = row0 + threadIdx.x; i < row1; i += blockDim.x) {
@@ -344,14 +369,9 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_mixed_kernel(MixedArgs A)
                 }
             }
         }
-        {
-            double v[2] = {gpart, rpart};
-            cta_sum<2>(v, s_part, s_tot);
-            if (threadIdx.x == 0) {
-                npart[0 * mg + blockIdx.x] = v[0];
-                npart[1 * mg + blockIdx.x] = v[1];
-            }
-        }
+        s_gr[2 * threadIdx.x] = gpart;
+        s_gr[2 * threadIdx.x + 1] = rpart;
+        pending = true;
         if (!verify) ++it;
         if (!grid_sync(count, nblocks, epoch, A.status)) { ok = false; break; }
     }
