@@ -223,30 +223,17 @@ __device__ __forceinline__ void reduced_m32(const Tet &t, double mu, double lam,
         }
 }
 
-// out = M v for the reduced Hessian, FP64, matrix-free.
-__device__ __forceinline__ void reduced_mv(const Tet &t, double mu, double lam, const double v[9], double out[9])
+// Reduced Hessian M (9x9, index 3k+c), FP64, packed upper.
+__device__ __forceinline__ void reduced_m64(const Tet &t, double mu, double lam, double M[45])
 {
-    double Fv[3][3], Yv[3], YkVl[3][3];
 #pragma unroll
-    for (int l = 0; l < 3; ++l) {
+    for (int r = 0; r < 9; ++r)
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-            Fv[l][c] = t.FFt[c][0] * v[3 * l] + t.FFt[c][1] * v[3 * l + 1] + t.FFt[c][2] * v[3 * l + 2];
-        Yv[l] = t.Y[l][0] * v[3 * l] + t.Y[l][1] * v[3 * l + 1] + t.Y[l][2] * v[3 * l + 2];
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-            YkVl[k][l] = t.Y[k][0] * v[3 * l] + t.Y[k][1] * v[3 * l + 1] + t.Y[k][2] * v[3 * l + 2];
-    }
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            double acc = 0.0;
-#pragma unroll
-            for (int l = 0; l < 3; ++l)
-                acc += t.s[k][l] * v[3 * l + c] + mu * t.Y[l][c] * YkVl[k][l] + mu * t.om[k][l] * Fv[l][c] +
-                       lam * t.Y[k][c] * Yv[l];
-            out[3 * k + c] = t.V * acc;
+        for (int q = r; q < 9; ++q) {
+            const int k = r / 3, c = r % 3, l = q / 3, d = q % 3;
+            double v = mu * (t.Y[l][c] * t.Y[k][d] + t.FFt[c][d] * t.om[k][l]) + lam * t.Y[k][c] * t.Y[l][d];
+            if (c == d) v += t.s[k][l];
+            M[pk(r, q)] = t.V * v;
         }
 }
 
@@ -403,14 +390,22 @@ __device__ int refine64(const Tet &t, double mu, double lam, const Slots &sl, bo
 #pragma unroll
         for (int r = 0; r < 9; ++r) sl.u(r, j) *= inv;
     }
-    // A = U^T M U
+    // A = U^T M U with M formed once (45 entries): M u_j is 81 FMAs
+    double M[45];
+    reduced_m64(t, mu, lam, M);
     double scale = 0.0;
 #pragma unroll 1
     for (int j = 0; j < 9; ++j) {
         double v[9], mv[9];
 #pragma unroll
         for (int r = 0; r < 9; ++r) v[r] = sl.u(r, j);
-        reduced_mv(t, mu, lam, v, mv);
+#pragma unroll
+        for (int r = 0; r < 9; ++r) {
+            double acc = 0.0;
+#pragma unroll
+            for (int q = 0; q < 9; ++q) acc = fma(M[pk(r, q)], v[q], acc);
+            mv[r] = acc;
+        }
         for (int i = 0; i <= j; ++i) {
             double d = 0.0;
 #pragma unroll
@@ -1081,7 +1076,6 @@ __global__ void __launch_bounds__(kRefineThreads) vjp_pass2_kernel(
         {
             Tet t;
             tet_eval(X, x, mu, lam, t);
-            refine64(t, mu, lam, sl, true, es, e);
 #pragma unroll
             for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -1092,6 +1086,7 @@ __global__ void __launch_bounds__(kRefineThreads) vjp_pass2_kernel(
                         ff6[sym3(i, j)] = t.FFt[i][j];
                     }
                 }
+            refine64(t, mu, lam, sl, true, es, e);
         }
         // eigenvalues (A's diagonal), a = U^T lh and b = U^T dh, then into
         // slots 81..107 and om, FFt into 108..119 once every diagonal entry of
