@@ -345,6 +345,22 @@ __device__ __forceinline__ void store_eig(const EigStore &es, int64_t e, const f
     for (int q = 0; q < kEigRec / 4; ++q) dst[q] = make_float4(rec[4 * q], rec[4 * q + 1], rec[4 * q + 2], rec[4 * q + 3]);
 }
 
+// Pass 1 parks every tet's FP32 reduced Hessian (45 floats, padded to 48) in
+// the tet's record slot for the classification kernel; NaN in the first word
+// marks a tet pass 1 rejected (bad index or non-finite element).
+__device__ __forceinline__ void store_m32(const EigStore &es, int64_t e, const float A[45], bool valid)
+{
+    float4 *dst = reinterpret_cast<float4 *>(es.base + e * kEigRec);
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+        float v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = 4 * q + k < 45 ? A[4 * q + k] : 0.f;
+        if (q == 0 && !valid) v[0] = __int_as_float(0x7fc00000);
+        dst[q] = make_float4(v[0], v[1], v[2], v[3]);
+    }
+}
+
 // FP64 refinement of a tet's FP32 eigenbasis (the pairs pass 1 stored).
 // Orders the flagged eigenvalues first, re-orthonormalises U in FP64
 // (modified Gram-Schmidt), forms A = U^T M U and runs FP64 Jacobi sweeps
@@ -592,13 +608,12 @@ __global__ void __launch_bounds__(128) elem_pass1_kernel(int32_t n, int64_t nt, 
                                                          const int32_t *__restrict__ col, int64_t nnzb,
                                                          const double *__restrict__ Xr, const double *__restrict__ xc,
                                                          const double *__restrict__ E, double nu, double *fine_val,
-                                                         double *g, int32_t *hdr, uint8_t *mcode, EigStore es,
-                                                         uint32_t *status)
+                                                         double *g, EigStore es, uint32_t *status)
 {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nt; e += (int64_t)gridDim.x * blockDim.x) {
         int vid[4];
         double X[4][3], x[4][3];
-        int flag = 0;
+        bool parked = false;
         if (!load_tet(tets, e, n, Xr, xc, vid, X, x)) {
             set_status(status, ST_BAD_INDEX);
         } else {
@@ -650,12 +665,42 @@ __global__ void __launch_bounds__(128) elem_pass1_kernel(int32_t n, int64_t nt, 
                                   },
                                   status);
                 }
-                float A32[45], U32[9][9];
+                float A32[45];
                 reduced_m32(t, mu, lam, A32);
-                jacobi9f(A32, U32);
-                flag = flagged_count(A32);
-                if (flag > 0) store_eig(es, e, A32, U32);
+                store_m32(es, e, A32, true);
+                parked = true;
             }
+        }
+        if (!parked) {
+            float z[45] = {};
+            store_m32(es, e, z, false);
+        }
+    }
+}
+
+// FP32 eigen-classification of every tet's reduced Hessian parked by pass 1
+// (cyclic Jacobi), flagged tets' eigenpair records written over the parked
+// matrix, counts for the worklist.  Kept apart from the FP64 element work so
+// that each kernel's instruction stream stays small.
+__global__ void __launch_bounds__(128) classify_kernel(int64_t nt, EigStore es, int32_t *hdr, uint8_t *mcode)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nt; e += (int64_t)gridDim.x * blockDim.x) {
+        const float4 *src = reinterpret_cast<const float4 *>(es.base + e * kEigRec);
+        float A[48];
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+            const float4 v = src[q];
+            A[4 * q] = v.x;
+            A[4 * q + 1] = v.y;
+            A[4 * q + 2] = v.z;
+            A[4 * q + 3] = v.w;
+        }
+        int flag = 0;
+        if (!isnan(A[0])) {
+            float U[9][9];
+            jacobi9f(A, U);
+            flag = flagged_count(A);
+            if (flag > 0) store_eig(es, e, A, U);
         }
         mcode[e] = (uint8_t)flag;
         count_flag(hdr, flag);
@@ -998,12 +1043,12 @@ __global__ void __launch_bounds__(128) vjp_pass1_kernel(int32_t n, int64_t nt, c
                                                         const double *__restrict__ E, double nu,
                                                         const double *__restrict__ lam_f, const double *__restrict__ dx,
                                                         double *__restrict__ dL_dE, double *dL_dX,
-                                                        int32_t *hdr, uint8_t *mcode, EigStore es, uint32_t *status)
+                                                        EigStore es, uint32_t *status)
 {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nt; e += (int64_t)gridDim.x * blockDim.x) {
         int vid[4];
         double X[4][3], x[4][3];
-        int flag = 0;
+        bool parked = false;
         if (!load_tet(tets, e, n, Xr, xc, vid, X, x)) {
             set_status(status, ST_BAD_INDEX);
             dL_dE[e] = 0.0;
@@ -1025,14 +1070,15 @@ __global__ void __launch_bounds__(128) vjp_pass1_kernel(int32_t n, int64_t nt, c
             for (int a = 0; a < 4; ++a)
 #pragma unroll
                 for (int c = 0; c < 3; ++c) atomicAdd(dL_dX + 3 * (int64_t)vid[a] + c, -Xb[a][c]);
-            float A32[45], U32[9][9];
+            float A32[45];
             reduced_m32(t, mu, lam, A32);
-            jacobi9f(A32, U32);
-            flag = flagged_count(A32);
-            if (flag > 0) store_eig(es, e, A32, U32);
+            store_m32(es, e, A32, true);
+            parked = true;
         }
-        mcode[e] = (uint8_t)flag;
-        count_flag(hdr, flag);
+        if (!parked) {
+            float z[45] = {};
+            store_m32(es, e, z, false);
+        }
     }
 }
 
@@ -1334,8 +1380,9 @@ extern "C" int agipc_fine_assemble_stvk(agipc_ctx *ctx, int32_t n_fine, int64_t 
         if (cudaMemsetAsync(ws, 0, kHdr * sizeof(int32_t), st) != cudaSuccess) return AGIPC_ERR_CUDA;
         const EigStore es{reinterpret_cast<float *>(ws + eig_offset_words(n_tets)), n_tets};
         elem_pass1_kernel<<<(unsigned)min64(div_up(n_tets, 128), (int64_t)ctx->num_sms * 16), 128, 0, st>>>(
-            n_fine, n_tets, tets, fine_row_ptr, fine_col, fine_nnzb, X_rest, x, E, nu, fine_val, g, ws, mcode, es,
-            ctx->status);
+            n_fine, n_tets, tets, fine_row_ptr, fine_col, fine_nnzb, X_rest, x, E, nu, fine_val, g, es, ctx->status);
+        classify_kernel<<<(unsigned)min64(div_up(n_tets, 128), (int64_t)ctx->num_sms * 16), 128, 0, st>>>(
+            n_tets, es, ws, mcode);
         bucket_scatter_kernel<<<(unsigned)min64(div_up(n_tets, 256), (int64_t)ctx->num_sms * 8), 256, 0, st>>>(
             n_tets, mcode, ws, list);
         elem_pass2_kernel<<<(unsigned)min64(div_up(n_tets, kRefineThreads), (int64_t)ctx->num_sms * 7),
@@ -1364,7 +1411,9 @@ extern "C" int agipc_stvk_vjp(agipc_ctx *ctx, int32_t n_fine, int64_t n_tets, co
         if (cudaMemsetAsync(ws, 0, kHdr * sizeof(int32_t), st) != cudaSuccess) return AGIPC_ERR_CUDA;
         const EigStore es{reinterpret_cast<float *>(ws + eig_offset_words(n_tets)), n_tets};
         vjp_pass1_kernel<<<(unsigned)min64(div_up(n_tets, 128), (int64_t)ctx->num_sms * 16), 128, 0, st>>>(
-            n_fine, n_tets, tets, X_rest, x, E, nu, lam, dx, dL_dE, dL_dX_rest, ws, mcode, es, ctx->status);
+            n_fine, n_tets, tets, X_rest, x, E, nu, lam, dx, dL_dE, dL_dX_rest, es, ctx->status);
+        classify_kernel<<<(unsigned)min64(div_up(n_tets, 128), (int64_t)ctx->num_sms * 16), 128, 0, st>>>(
+            n_tets, es, ws, mcode);
         bucket_scatter_kernel<<<(unsigned)min64(div_up(n_tets, 256), (int64_t)ctx->num_sms * 8), 256, 0, st>>>(
             n_tets, mcode, ws, list);
         vjp_pass2_kernel<<<(unsigned)min64(div_up(n_tets, kRefineThreads), (int64_t)ctx->num_sms * 7),
