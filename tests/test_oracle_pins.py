@@ -253,7 +253,7 @@ def test_fine_pcg_matches_scipy_cg(unit_cube_scene):
     dinv = oracle.block_jacobi(crp, cci, cval)
     x, it, rr, conv = oracle.pcg(crp, cci, cval, dinv, -sc.g, 1e-12, 10000)
     A = scipy.sparse.csr_matrix(dense_from_bsr(crp, cci, cval))
-    Mb = scipy.sparse.block_diag([d for d in dinv]).tocsr()
+    Mb = scipy.sparse.block_diag([scipy.sparse.csr_array(d) for d in dinv], format="csr")
     xs, info = scipy.sparse.linalg.cg(A, -sc.g.ravel(), M=Mb, rtol=1e-12, maxiter=10000)
     assert conv and info == 0
     assert np.linalg.norm(x.ravel() - xs) <= 1e-9 * np.linalg.norm(xs)
