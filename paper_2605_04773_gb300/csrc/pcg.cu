@@ -359,9 +359,21 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_kernel(PcgArgs A)
                 if (it == 0) {
                     alpha = g / dl;
                 } else {
+                    // beta = g / gamma_old and alpha = g t / den share one
+                    // division by gamma_old den (an FP64 division is a long
+                    // dependent chain here); the two quotients are used when
+                    // that product leaves the normal range
                     const double t = gamma_old * alpha_old;
-                    beta = g / gamma_old;
-                    alpha = (g * t) / fma(dl, t, -g * g);
+                    const double den = fma(dl, t, -g * g);
+                    const double q = gamma_old * den;
+                    if (fabs(q) >= 2.2250738585072014e-308 && fabs(q) <= 1.0e300) {
+                        const double inv = 1.0 / q;
+                        beta = g * den * inv;
+                        alpha = g * t * gamma_old * inv;
+                    } else {
+                        beta = g / gamma_old;
+                        alpha = (g * t) / den;
+                    }
                 }
                 if (!isfinite(alpha) || !isfinite(beta)) decision = 3;
                 gamma_old = g;
