@@ -232,21 +232,20 @@ def run_ours(args):
     ctx.check()
     fres = fine.host()
 
-    # ---- end to end: host buffers, H2D of every input and D2H of dx per step
-    host_in = {k: getattr(ds, k).cpu().pin_memory() for k in ("edges", "tags", "row_ptr", "col", "val", "pair_idx",
-                                                                "pair_blk", "g")}
+    # ---- end to end: host buffers, H2D of every input and D2H of dx per step,
+    # through the serving pipeline (step k+1's copies overlap step k)
+    host_in = {k: getattr(ds, k).cpu().pin_memory() for k in agipc.SCENE_INPUTS}
     h2d = sum(t.numel() * t.element_size() for t in host_in.values())
     dx_host = torch.empty_like(step.dx, device="cpu").pin_memory()
     d2h = dx_host.numel() * dx_host.element_size()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pipe = agipc.HostPipeline(ctx, (ds, agipc.DeviceScene(sc, dev)), tol=TOL)
     e2e_steps = max(3, min(10, args.steps))
+    pipe.run([host_in] * 2, [dx_host] * 2)   # warm-up of the second buffer set
     torch.cuda.synchronize(dev)
+    ctx.check()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(e2e_steps):
-        for k, t in host_in.items():
-            getattr(ds, k).copy_(t, non_blocking=True)
-        one()
-        dx_host.copy_(step.dx, non_blocking=True)
+    pipe.run([host_in] * e2e_steps, [dx_host] * e2e_steps)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     e2e_s = e0.elapsed_time(e1) / 1e3

@@ -374,6 +374,61 @@ class CoarsenedStep:
                     relres=float(self.relres.item()))
 
 
+SCENE_INPUTS = ("edges", "tags", "row_ptr", "col", "val", "pair_idx", "pair_blk", "g")
+
+
+class HostPipeline:
+    """Coarsened steps whose inputs arrive in pinned host memory, one after
+    another, as a serving loop runs them: two sets of device input buffers;
+    the host-to-device copies of step k+1 run on a copy stream while step k's
+    kernels run on the context's stream, and each step's dx is copied back
+    to the host.  Both steps share the context (their kernels are ordered on
+    its stream)."""
+
+    def __init__(self, ctx: Context, buffers, tol: float, max_iter: int = 100000):
+        if len(buffers) != 2:
+            raise ValueError("two DeviceScene buffers are needed")
+        self.ctx = ctx
+        self.bufs = tuple(buffers)
+        self.steps = [CoarsenedStep(ctx, b, tol, max_iter) for b in self.bufs]
+        self.copy_stream = torch.cuda.Stream(device=self.bufs[0].g.device)
+        self.copied = [torch.cuda.Event() for _ in range(2)]
+        self.free = [torch.cuda.Event() for _ in range(2)]
+
+    def run(self, host_inputs, dx_out):
+        """Enqueue len(host_inputs) steps.  host_inputs[k] maps every name of
+        SCENE_INPUTS to a pinned CPU tensor shaped like the DeviceScene's;
+        dx_out[k] is a pinned CPU tensor [n, 3] that receives step k's dx.
+        Asynchronous: synchronize (or read the context's status) before using
+        dx_out."""
+        comp = self.ctx.stream
+        n = len(host_inputs)
+        if len(dx_out) != n:
+            raise ValueError("one dx buffer per step")
+        for e in self.free:
+            e.record(comp)
+
+        def issue(k):
+            i = k % 2
+            self.copy_stream.wait_event(self.free[i])
+            with torch.cuda.stream(self.copy_stream):
+                for f in SCENE_INPUTS:
+                    getattr(self.bufs[i], f).copy_(host_inputs[k][f], non_blocking=True)
+            self.copied[i].record(self.copy_stream)
+
+        if n:
+            issue(0)
+        for k in range(n):
+            i = k % 2
+            if k + 1 < n:
+                issue(k + 1)
+            comp.wait_event(self.copied[i])
+            self.steps[i].run()
+            with torch.cuda.stream(comp):
+                dx_out[k].copy_(self.steps[i].dx, non_blocking=True)
+            self.free[i].record(comp)
+
+
 class MixedDeviceScene(DeviceScene):
     """DeviceScene plus the precision form's inputs (FP32 blocks and stencils,
     FP64 small-gap stencils)."""

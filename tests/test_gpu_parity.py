@@ -228,6 +228,35 @@ def test_fine_arm_full_size(domino_full):
 # ------------------------------------------------------------------ status / edge cases
 
 
+def test_host_pipeline_matches_single_steps():
+    """Steps fed from pinned host buffers through the two-buffer pipeline give
+    the dx of plain steps on the same inputs (and every step's own inputs:
+    the right-hand sides differ from step to step)."""
+    sc = scenes.unit_cube(seed=1001)
+    a, b = agipc.DeviceScene(sc), agipc.DeviceScene(sc)
+    ctx = a.context()
+    base = {f: getattr(a, f).cpu() for f in agipc.SCENE_INPUTS}
+    host, outs = [], []
+    for s in (1.0, 2.0, -0.5, 3.0):
+        d = {f: t.clone().pin_memory() for f, t in base.items()}
+        d["g"] = (base["g"] * s).pin_memory()
+        host.append(d)
+        outs.append(torch.empty(sc.n, 3, dtype=torch.float64).pin_memory())
+    pipe = agipc.HostPipeline(ctx, (a, b), tol=1e-12)
+    pipe.run(host, outs)
+    torch.cuda.synchronize()
+    assert ctx.status() == agipc.OK
+    ref = agipc.DeviceScene(sc)
+    step = agipc.CoarsenedStep(ctx, ref, tol=1e-12)
+    for k, d in enumerate(host):
+        ref.g.copy_(d["g"])
+        step.run()
+        want = step.dx.cpu()
+        assert ctx.status() == agipc.OK
+        assert torch.abs(outs[k] - want).max() <= 1e-10 * torch.abs(want).max()
+    ctx.close()
+
+
 def test_status_not_converged_and_zero_rhs():
     sc = scenes.unit_cube(seed=1001)
     ds = agipc.DeviceScene(sc)
