@@ -10,7 +10,7 @@
  *   agipc_pcg              H_c y = -g_c by block-Jacobi PCG      (Algorithm 1; Sec. 5, Preconditioners)
  *   agipc_prolongate       dx = U^T y                            (Sec. 4.3)
  *
- * plus the precision form (agipc_*_mixed), the differentiation form
+ * plus the precision form (agipc_precision_split, agipc_*_mixed), the differentiation form
  * (agipc_fine_assemble_stvk, agipc_restrict, agipc_stvk_vjp), the batched
  * form (agipc_batch_coarse_offsets, agipc_pcg_batched) and
  * agipc_prolongate_add, agipc_aggregate_static.
@@ -176,6 +176,27 @@ int agipc_assemble_coarse_mixed(agipc_ctx *ctx, int32_t n_fine, const int32_t *l
                                 const double *pair_blk64, const double *g, int32_t *coarse_row_ptr,
                                 int32_t *coarse_col, double *coarse_val, float *coarse_val32, int64_t coarse_cap_nnzb,
                                 int32_t *coarse_nnzb_dev, double *g_c, float *dinv32);
+
+/*
+ * Inputs of the precision form from the FP64 ones (the paper computes in
+ * FP64, Sec. 5; the precision form keeps only the barrier terms at small gap
+ * distances in FP64, whose stiffness grows like (dhat/d)^2):
+ *   val [fine_nnzb][9] FP64       -> val32 [fine_nnzb][9]: FP32 rounding (nearest even)
+ *   pair_idx [P][4], pair_blk [P][90] FP64, pair_gap [P] FP64 (the stencils' gaps d)
+ *   gap_limit (host)              stencils with gap < gap_limit stay FP64
+ *   pair_idx32 [P][4], pair_blk32 [P][90] FP32   out: the other stencils, rounded
+ *   pair_idx64 [P][4], pair_blk64 [P][90] FP64   out: the small-gap stencils, copied
+ *   counts_dev  out: device int32[2] = {stencils in the FP32 list, in the FP64 list}
+ * Each output list must have room for all P stencils; both keep the input
+ * order.  The two counts are the n_pairs32 and n_pairs64 that
+ * agipc_assemble_coarse_mixed takes on the host: read them once (one copy)
+ * after this call.  Uses the context's assembly scratch, which the next
+ * assembly overwrites.  The decision gap < gap_limit is an FP64 comparison.
+ */
+int agipc_precision_split(agipc_ctx *ctx, int64_t fine_nnzb, const double *val, float *val32, int64_t n_pairs,
+                          const int32_t *pair_idx, const double *pair_blk, const double *pair_gap, double gap_limit,
+                          int32_t *pair_idx32, float *pair_blk32, int32_t *pair_idx64, double *pair_blk64,
+                          int32_t *counts_dev);
 
 /*
  * Precision form of the PCG: the 3x3 blocks (val32), the SpMV and the
@@ -408,9 +429,13 @@ int64_t agipc_stvk_workspace_bytes(int64_t n_tets);
  * buffers (about 12 MiB) compiled into the library's device image, so every
  * GPU that loads the library holds it until the process exits.  n_fine above
  * that maximum is rejected with AGIPC_ERR_INVALID_ARG before anything is
- * enqueued.  The first call on a device looks the array's device address up
- * (cudaGetSymbolAddress) and caches it; make that first call before any
- * stream capture.  The call never calls cudaMalloc or cudaFree.  All calls
+ * enqueued.  Every call made outside stream capture looks the array's device
+ * address up (cudaGetSymbolAddress) for the current device and remembers it;
+ * a call made while cuda_stream is being captured reuses the remembered
+ * address.  So the first call on a device must come before any stream
+ * capture, and after cudaDeviceReset (which unloads the array) one call
+ * outside capture must come before the next captured one.  The call never
+ * calls cudaMalloc or cudaFree.  All calls
  * share the one array: calls that overlap on the GPU (different streams, no
  * ordering between them) race and corrupt each other's results; serialize
  * them.  The array keeps the previous call's contents, which no call reads.

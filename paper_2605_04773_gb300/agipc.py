@@ -72,6 +72,7 @@ def load():
                                                 P, P, P]
     lib.agipc_pcg_mixed.argtypes = [P, i32, P, P, P, P, P, P, P, P, ctypes.POINTER(_PcgOptions), i32, P, P]
     f64 = ctypes.c_double
+    lib.agipc_precision_split.argtypes = [P, i64, P, P, i64, P, P, P, f64, P, P, P, P, P]
     D3 = ctypes.POINTER(ctypes.c_double)
     lib.agipc_prolongate_add.argtypes = [P, i32, P, P, P, P]
     lib.agipc_fine_assemble_stvk.argtypes = [P, i32, i64, P, P, P, D3, P, f64, P, P, P, P, i64, P, P, P, i64]
@@ -92,7 +93,7 @@ def load():
     lib.agipc_status_string.restype = ctypes.c_char_p
     for name in ("agipc_create", "agipc_destroy", "agipc_set_stream", "agipc_aggregate", "agipc_assemble_coarse",
                  "agipc_pcg", "agipc_prolongate", "agipc_status", "agipc_aggregate_static",
-                 "agipc_assemble_coarse_mixed", "agipc_pcg_mixed", "agipc_prolongate_add", "agipc_fine_assemble_stvk",
+                 "agipc_assemble_coarse_mixed", "agipc_pcg_mixed", "agipc_precision_split", "agipc_prolongate_add", "agipc_fine_assemble_stvk",
                  "agipc_restrict", "agipc_stvk_vjp", "agipc_batch_coarse_offsets", "agipc_pcg_batched", "agipc_strain_tags", "agipc_affine_plan", "agipc_assemble_affine",
                  "agipc_prolongate_affine", "agipc_stvk_energy", "agipc_max_abs"):
         getattr(lib, name).restype = ctypes.c_int
@@ -186,6 +187,14 @@ def agipc_pcg(ctx: Context, max_rows: int, n_rows_dev, row_ptr, col, val, dinv, 
 
 def agipc_prolongate(ctx: Context, n_fine: int, labels, y, dx):
     _check(load().agipc_prolongate(ctx.handle, int(n_fine), _ptr(labels), _ptr(y), _ptr(dx)), "agipc_prolongate")
+
+
+def agipc_precision_split(ctx: Context, val, val32, pair_idx, pair_blk, pair_gap, gap_limit: float, pair_idx32,
+                          pair_blk32, pair_idx64, pair_blk64, counts_dev):
+    _check(load().agipc_precision_split(
+        ctx.handle, int(val.shape[0]), _ptr(val), _ptr(val32), int(pair_idx.shape[0]), _ptr(pair_idx),
+        _ptr(pair_blk), _ptr(pair_gap), float(gap_limit), _ptr(pair_idx32), _ptr(pair_blk32), _ptr(pair_idx64),
+        _ptr(pair_blk64), _ptr(counts_dev)), "agipc_precision_split")
 
 
 def agipc_assemble_coarse_mixed(ctx: Context, n_fine: int, labels, n_coarse_dev, fine_row_ptr, fine_col, fine_val32,
@@ -430,19 +439,31 @@ class HostPipeline:
 
 
 class MixedDeviceScene(DeviceScene):
-    """DeviceScene plus the precision form's inputs (FP32 blocks and stencils,
-    FP64 small-gap stencils)."""
+    """DeviceScene plus the precision form's inputs, made on the GPU by
+    agipc_precision_split from the FP64 blocks, stencils and gaps: FP32 fine
+    blocks and stencils, FP64 stencils of gaps below fp64_gap * dhat."""
 
     def __init__(self, sc, device="cuda", fp64_gap: float = 0.05):
         super().__init__(sc, device)
-        from . import scenes
-        pi = scenes.precision_inputs(sc, fp64_gap)
-        t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(device=device, dtype=dt)  # noqa: E731
-        self.val32 = t(pi["val32"].reshape(-1, 9), torch.float32)
-        self.pair_idx32 = t(pi["pair_idx32"].reshape(-1, 4), torch.int32)
-        self.pair_blk32 = t(pi["pair_blk32"].reshape(-1, 90), torch.float32)
-        self.pair_idx64 = t(pi["pair_idx64"].reshape(-1, 4), torch.int32)
-        self.pair_blk64 = t(pi["pair_blk64"].reshape(-1, 90), torch.float64)
+        dev = self.g.device
+        P = int(self.pair_idx.shape[0])
+        gap = np.asarray(sc.meta["pair_d"], dtype=np.float64) if P else np.zeros(0)
+        self.pair_gap = torch.from_numpy(np.ascontiguousarray(gap)).to(device=dev)
+        self.gap_limit = float(fp64_gap) * float(sc.meta["dhat"])
+        self.val32 = torch.empty(self.val.shape[0], 9, device=dev, dtype=torch.float32)
+        idx32 = torch.empty(P, 4, device=dev, dtype=torch.int32)
+        blk32 = torch.empty(P, 90, device=dev, dtype=torch.float32)
+        idx64 = torch.empty(P, 4, device=dev, dtype=torch.int32)
+        blk64 = torch.empty(P, 90, device=dev, dtype=torch.float64)
+        counts = torch.zeros(2, device=dev, dtype=torch.int32)
+        ctx = self.context()
+        agipc_precision_split(ctx, self.val, self.val32, self.pair_idx, self.pair_blk, self.pair_gap, self.gap_limit,
+                              idx32, blk32, idx64, blk64, counts)
+        ctx.check()
+        ctx.close()
+        n32, n64 = (int(c) for c in counts.cpu())
+        self.pair_idx32, self.pair_blk32 = idx32[:n32], blk32[:n32]
+        self.pair_idx64, self.pair_blk64 = idx64[:n64], blk64[:n64]
 
 
 class MixedStep(CoarsenedStep):
@@ -473,6 +494,27 @@ class MixedStep(CoarsenedStep):
         out["val32"] = self.val32[:nnz].cpu().numpy().reshape(-1, 3, 3)
         out["dinv32"] = self.dinv32[:out["n_c"]].cpu().numpy().reshape(-1, 3, 3)
         return out
+
+
+class MixedFineStep:
+    """The fine system (identity labels, contacts merged) solved in the
+    precision form: FP32 blocks, SpMV and preconditioner, FP64 dots and
+    residual replacement against the FP64 master."""
+
+    def __init__(self, ctx: Context, ds: MixedDeviceScene, tol: float, max_iter: int = 100000,
+                 refine_every: int = 20):
+        self.inner = MixedStep(ctx, ds, tol, max_iter, refine_every)
+        self.inner.labels.copy_(torch.arange(ds.n, dtype=torch.int32, device=ds.g.device))
+        self.inner.n_c.fill_(ds.n)
+
+    def assemble(self):
+        self.inner.assemble()
+
+    def solve(self):
+        self.inner.solve()
+
+    def host(self):
+        return self.inner.host()
 
 
 class PostCoarsening:

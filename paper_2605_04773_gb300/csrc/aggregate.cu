@@ -201,11 +201,17 @@ extern "C" int agipc_aggregate_static(void *cuda_stream, int32_t n_fine, int64_t
     if (((uintptr_t)edges & 7u) != 0) return AGIPC_ERR_INVALID_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return AGIPC_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &capture) != cudaSuccess) return AGIPC_ERR_CUDA;
     int32_t *scratch = nullptr;
     {
-        // first call on this device: look the array's device address up once
+        // Outside capture the address is looked up afresh (a device reset
+        // reloads the array elsewhere); under capture the last one is reused,
+        // since the lookup may load the module, which capture forbids.
         std::lock_guard<std::mutex> lock(g_static_agg_mutex);
-        if (!g_static_agg_ptr[dev]) {
+        if (capture == cudaStreamCaptureStatusNone || !g_static_agg_ptr[dev]) {
+            if (capture != cudaStreamCaptureStatusNone) return AGIPC_ERR_CUDA;
             void *p = nullptr;
             if (cudaGetSymbolAddress(&p, g_static_agg_scratch) != cudaSuccess || !p) return AGIPC_ERR_CUDA;
             g_static_agg_ptr[dev] = static_cast<int32_t *>(p);
@@ -216,7 +222,6 @@ extern "C" int agipc_aggregate_static(void *cuda_stream, int32_t n_fine, int64_t
     uint32_t *ghash = reinterpret_cast<uint32_t *>(scratch + kStaticAggNodes);
     int32_t *rank = scratch + 2 * kStaticAggNodes;
     int32_t *parts = scratch + 3 * kStaticAggNodes + 1;
-    cudaStream_t st = (cudaStream_t)cuda_stream;
     // The array keeps the previous call's contents; every word this call
     // reads is written by this call first, and the status starts at zero.
     if (cudaMemsetAsync(status_dev, 0, sizeof(uint32_t), st) != cudaSuccess) return AGIPC_ERR_CUDA;

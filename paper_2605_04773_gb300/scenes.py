@@ -526,19 +526,6 @@ def tiny_box(seed: int, nx: int = 1, ny: int = 1, nz: int = 1, n_pairs: int = 2,
                        dhat=dhat, pair_fn=fn, keep_elements=True)
 
 
-def precision_inputs(sc: Scene, fp64_gap: float = 0.05) -> dict:
-    """Inputs of the precision form: the fine blocks and the barrier stencils
-    rounded to FP32, except the stencils whose gap is below fp64_gap * dhat,
-    which stay FP64 (their stiffness grows like (dhat/d)^2)."""
-    d = np.asarray(sc.meta["pair_d"]) if sc.n_pairs else np.zeros(0)
-    small = d < fp64_gap * sc.meta["dhat"]
-    return dict(val32=sc.val.astype(np.float32),
-                pair_idx32=np.ascontiguousarray(sc.pair_idx[~small]),
-                pair_blk32=np.ascontiguousarray(sc.pair_blk[~small].astype(np.float32)),
-                pair_idx64=np.ascontiguousarray(sc.pair_idx[small]),
-                pair_blk64=np.ascontiguousarray(sc.pair_blk[small]))
-
-
 def _no_pairs(rng, body_info):
     return np.zeros((0, 4), np.int32), np.zeros((0, 12)), np.zeros(0), 1.0
 

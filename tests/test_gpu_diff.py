@@ -128,6 +128,58 @@ def test_full_size_gradient_matches_oracle(diff_grid_run):
     assert np.all(np.abs(got["dX"][verts] - ad["dL_dX"][verts]) <= 1e-5 * sX + trunc)
 
 
+def test_full_size_adjoint_matches_central_differences_of_L(diff_grid_run):
+    # dL/dE and dL/dX_rest from the adjoint re-solve against central
+    # differences of L = |x_next - x_target|^2 itself, each L evaluated by the
+    # GPU forward step (fine StVK assembly, the same labels, coarse assembly,
+    # PCG to 1e-12, prolongation) on the 46^3 grid.  A single tet moves L by
+    # about 3.5e-13 of its value when its E changes by 1e-6, below the FP64
+    # rounding noise of the solve, so the differences are taken along
+    # directions over many parameters at once: d = E o sign(dL/dE) on all
+    # tets and on three random halves of them (eps = 1e-6 relative), and
+    # d = cell o sign(dL/dX) on all rest coordinates and a random half (eps =
+    # 1e-7).  Scaling E leaves the PSD clamp's eigenvectors unchanged, so L is
+    # smooth along the E directions.
+    agipc = _agipc()
+    pr, _ = diff_grid_run
+    dp = agipc.DiffDeviceProblem(pr)
+    ctx = dp.context()
+    dev = dp.x.device
+    step = agipc.DiffStep(ctx, dp, tol=1e-12)
+    xt = torch.tensor(pr["x_target"], dtype=torch.float64, device=dev)
+    X0 = torch.tensor(pr["X_rest"], dtype=torch.float64, device=dev)
+    E0 = torch.tensor(pr["E"], dtype=torch.float64, device=dev)
+
+    def L_of(E, X):
+        d = (step.forward(E, X) - xt).reshape(-1)
+        assert ctx.status() == agipc.OK
+        return float(torch.dot(d, d).item())
+
+    v = 2 * (step.forward(E0, X0) - xt)
+    step.backward(v)
+    assert ctx.status() == agipc.OK
+    dE, dX = step.dL_dE.clone(), step.dL_dX.clone()
+    rng = np.random.default_rng(31)
+    cell = 1.0 / 46
+    dirs_E = [torch.sign(dE) * E0]
+    for _ in range(3):
+        mask = torch.tensor(rng.random(dE.numel()) < 0.5, device=dev)
+        dirs_E.append(torch.sign(dE) * E0 * mask)
+    for d in dirs_E:
+        eps = 1e-6
+        fd = (L_of(E0 + eps * d, X0) - L_of(E0 - eps * d, X0)) / (2 * eps)
+        adj = float(torch.dot(dE, d).item())
+        assert abs(fd - adj) <= 1e-5 * abs(adj), (fd, adj)
+    dirs_X = [torch.sign(dX) * cell,
+              torch.sign(dX) * cell * torch.tensor(rng.random(dX.shape) < 0.5, device=dev)]
+    for d in dirs_X:
+        eps = 1e-7
+        fd = (L_of(E0, X0 + eps * d) - L_of(E0, X0 - eps * d)) / (2 * eps)
+        adj = float(torch.dot(dX.reshape(-1), d.reshape(-1)).item())
+        assert abs(fd - adj) <= 1e-5 * abs(adj), (fd, adj)
+    ctx.close()
+
+
 def test_bad_tet_index_sets_status():
     agipc = _agipc()
     sc = scenes.tiny_box(seed=10, nx=1, ny=1, nz=1, n_pairs=0)

@@ -14,6 +14,7 @@ import pytest
 import torch
 
 import oracle
+from oracle import precision
 from paper_2605_04773_gb300 import agipc, scenes
 
 pytestmark = pytest.mark.gpu
@@ -45,7 +46,7 @@ def _mixed(sc, tol):
 
 
 def _check(sc, got, tol):
-    pi = scenes.precision_inputs(sc)
+    pi = precision.scene_split(sc)
     lab, nc = oracle.labels(sc.n, sc.edges, sc.tags)
     assert got["n_c"] == nc and np.array_equal(got["labels"], lab)
     pidx = np.concatenate([pi["pair_idx32"], pi["pair_idx64"]])
@@ -76,7 +77,7 @@ def test_precision_form_unit_cube():
 
 def test_precision_form_domino_with_small_gaps():
     sc = scenes.domino_grid(seed=1003, gx=3, gy=3, dims=(4, 8, 12), n_pairs=6000, small_gap_frac=0.02)
-    pi = scenes.precision_inputs(sc)
+    pi = precision.scene_split(sc)
     assert pi["pair_idx64"].shape[0] > 0
     rc, got = _mixed(sc, 1e-6)
     assert rc == agipc.OK
@@ -94,3 +95,63 @@ def test_precision_form_refinement_off_and_not_converged_status():
     st2.run()
     assert ctx.status() == agipc.OK
     ctx.close()
+
+
+@pytest.mark.parametrize("case", ["small_gaps", "no_small_gaps", "all_small", "no_pairs"])
+def test_precision_split_matches_oracle(case):
+    # agipc_precision_split against the oracle's rule, bit for bit: the same
+    # FP64 comparison gap < limit, round-to-nearest FP32 values, input order
+    # kept in both lists
+    if case == "no_pairs":
+        sc = scenes.tiny_box(seed=4, nx=2, ny=2, nz=2, n_pairs=0)
+    else:
+        sc = scenes.domino_grid(seed=1003, gx=2, gy=2, dims=(3, 6, 8), n_pairs=3000,
+                                small_gap_frac={"small_gaps": 0.05, "no_small_gaps": 0.0, "all_small": 1.0}[case])
+    want = precision.scene_split(sc)
+    ds = agipc.MixedDeviceScene(sc)
+    assert np.array_equal(ds.val32.cpu().numpy(), want["val32"].reshape(-1, 9))
+    for k, w in (("pair_idx32", want["pair_idx32"]), ("pair_blk32", want["pair_blk32"]),
+                 ("pair_idx64", want["pair_idx64"]), ("pair_blk64", want["pair_blk64"])):
+        got = getattr(ds, k).cpu().numpy()
+        assert got.shape[0] == w.shape[0], k
+        assert np.array_equal(got.reshape(w.shape), w), k
+    if case == "no_small_gaps":
+        assert want["pair_idx64"].shape[0] == 0
+    if case == "all_small":
+        assert want["pair_idx32"].shape[0] == 0
+
+
+def test_precision_form_c3_errors_vs_fp64_oracle():
+    # The precision form on the full C3 scene (the 64-box domino with 1 % of
+    # the gaps below 0.05 dhat) against the FP64 oracle on the unrounded
+    # inputs.  The paper fixes no bound (it is all FP64), so the bounds come
+    # from the FP32 storage: the true coarse residual with the unrounded H_c
+    # is at most the solve's residual with its FP64 master (1.05 tol) plus
+    # u |H_c|_abs |y| with u = 2^-24 (every FP32 input entry is within u of
+    # its FP64 value); dx and the energy decrease are printed for the record.
+    sc = scenes.domino_grid(seed=1003, small_gap_frac=0.01)
+    tol = 1e-6
+    rc, got = _mixed(sc, tol)
+    assert rc == agipc.OK
+    ref = oracle.coarsened_step(sc, tol=1e-12)
+    lab, nc = oracle.labels(sc.n, sc.edges, sc.tags)
+    crp, cci, cval = oracle.galerkin(lab, nc, sc.row_ptr, sc.col, sc.val, sc.pair_idx, sc.pair_blk)
+    _, _, mag = oracle.galerkin(lab, nc, sc.row_ptr, sc.col, np.abs(sc.val), sc.pair_idx, np.abs(sc.pair_blk))
+    gc = oracle.coarse_gradient(lab, nc, sc.g)
+    y = got["y"]
+    nb = np.linalg.norm(gc)
+    res = np.linalg.norm(oracle.spmv(crp, cci, cval, y) + gc) / nb
+    bound = 1.05 * tol + 2.0 ** -24 * np.linalg.norm(oracle.spmv(crp, cci, mag, np.abs(y))) / nb
+    assert res <= bound, (res, bound)
+    dx_err = np.linalg.norm(got["dx"] - ref["dx"]) / np.linalg.norm(ref["dx"])
+    rp, ci, fv = oracle.fine_system(sc)
+    g = sc.g.reshape(-1)
+
+    def decrease(dx):
+        return float(g @ dx.reshape(-1) + 0.5 * dx.reshape(-1) @ oracle.spmv(rp, ci, fv, dx).reshape(-1))
+
+    e_ref, e_got = decrease(ref["dx"]), decrease(got["dx"])
+    e_err = abs(e_got - e_ref) / abs(e_ref)
+    print("C3 vs FP64 oracle: coarse residual %.3e (bound %.3e), dx rel err %.3e, energy decrease rel err %.3e"
+          % (res, bound, dx_err, e_err))
+    assert dx_err < 1e-3 and e_err < 1e-6

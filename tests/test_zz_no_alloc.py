@@ -1,14 +1,16 @@
 """The allocation-free labeller, agipc_aggregate_static, for callers that
 cannot allocate GPU memory (they have no agipc_ctx, whose creation calls
 cudaMalloc).  Its scratch is a fixed array inside the library, shared by all
-calls.  Checked through the C ABI against agipc_aggregate on two calls in a
-row with different inputs, so a stale array from the first call must not
-leak into the second.  This file is collected last on purpose.
+calls.  Checked through the C ABI, bit for bit, against the CPU oracle's union-find
+labels and against agipc_aggregate, on two calls in a row with different
+inputs, so a stale array from the first call must not leak into the
+second.  This file is collected last on purpose.
 """
 import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2605_04773_gb300 import agipc, scenes
 
 pytestmark = pytest.mark.gpu
@@ -33,7 +35,7 @@ def _with_context(n, edges, tags):
     return labels.cpu().numpy(), int(nc.item())
 
 
-def test_static_labeller_matches_context_labeller_twice():
+def test_static_labeller_matches_oracle_and_context_labeller_twice():
     big = scenes.domino_grid(seed=77, gx=2, gy=2, dims=(3, 5, 8), n_pairs=0)
     small = scenes.unit_cube(seed=1001)
     rng = np.random.default_rng(12)
@@ -49,9 +51,12 @@ def test_static_labeller_matches_context_labeller_twice():
         agipc.agipc_aggregate_static(stream, n, edges, tags, labels, nc, status)
         torch.cuda.synchronize()
         ref_labels, ref_nc = _with_context(n, edges, tags)
+        or_labels, or_nc = oracle.labels(n, np.asarray(e), np.asarray(t))
+        got = labels.cpu().numpy()
         assert int(status.item()) == 0
-        assert int(nc.item()) == ref_nc
-        assert np.array_equal(labels.cpu().numpy(), ref_labels)
+        assert int(nc.item()) == or_nc == ref_nc
+        assert np.array_equal(got, or_labels)
+        assert np.array_equal(got, ref_labels)
 
 
 def test_static_labeller_rejects_sizes_beyond_its_array():
