@@ -62,6 +62,23 @@ def replica_throughput(ws: int, units_per_rank: int, seconds: float) -> float:
     return ws * units_per_rank / seconds
 
 
+def shard_instances(counts, ws: int, rank: int):
+    """Contiguous instance range [a, b) of rank `rank` when the batched form's
+    instances are split over ws GPUs with no exchange (instances are
+    independent problems): boundary k is the first instance whose vertex
+    prefix sum reaches k / ws of the total, so every rank holds about the
+    same number of vertices and the ranges tile 0 .. len(counts)."""
+    counts = np.asarray(counts, dtype=np.int64)
+    n = counts.size
+    if ws <= 1:
+        return 0, n
+    pre = np.concatenate([[0], np.cumsum(counts)])
+    total = pre[-1]
+    bounds = [0] + [int(np.searchsorted(pre, k * total / ws, side="left")) for k in range(1, ws)] + [n]
+    bounds = np.maximum.accumulate(np.minimum(bounds, n))
+    return int(bounds[rank]), int(bounds[rank + 1])
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -272,7 +289,7 @@ def run_ours(args):
         # ---- differentiation form (forward step + adjoint + per-tet VJP)
         diff = differentiation_form(dev, steps=min(args.steps, 10))
         # ---- batched form (256 uneven instances, one graph replay)
-        batched = batched_form(dev, steps=min(args.steps, 10), peak_gbs=_peaks()[0])
+        batched = batched_form(dev, steps=min(args.steps, 10), peak_gbs=_peaks()[0], ws=ws, rank=rank)
         # ---- the Newton loop with backtracking (fine assembly to line search)
         newton = newton_form(dev, steps=min(args.steps, 5))
 
@@ -597,14 +614,17 @@ def newton_form(dev, steps: int):
     return out
 
 
-def batched_form(dev, steps: int, peak_gbs: float, n_inst: int = 256):
+def batched_form(dev, steps: int, peak_gbs: float, n_inst: int = 256, ws: int = 1, rank: int = 0):
     """Time the batched form: 256 uneven instances (2k-60k vertices) in one
     CUDA-graph replay of aggregate -> offsets -> mixed assembly -> batched
-    PCG -> prolongation, with the autotuned slice width."""
+    PCG -> prolongation, with the autotuned slice width.  With ws > 1 ranks
+    each rank runs its contiguous share of the instances (no exchange); the
+    job's time is the slowest rank's."""
     import torch
     from paper_2605_04773_gb300 import agipc, scenes
     t0 = time.perf_counter()
-    batch = scenes.batch_instances(n_inst=n_inst)
+    first, last = shard_instances(scenes.instance_vertex_counts(n_inst=n_inst), ws, rank)
+    batch = scenes.batch_instances(n_inst=last - first, first=first)
     gen_s = time.perf_counter() - t0
     bd = agipc.BatchDevice(batch, dev)
     ctx = bd.context()
@@ -659,6 +679,12 @@ def batched_form(dev, steps: int, peak_gbs: float, n_inst: int = 256):
            "generator_s": gen_s, "graph": "one CUDA graph replay per batch",
            "workload": str(batch.n_inst) + " Kuhn-split hex grids, 2k-60k vertices log-uniform, random aspect, 30-90% collapsible, "
                        "0-5% of vertices in PT barrier stencils; FP32 blocks, FP64 accumulation, tol 1e-6"}
+    out["instance_range"] = [first, last]
+    if ws > 1:
+        # every rank solved its own instances; the job runs as long as its slowest rank
+        med_all = max_over_ranks([med_step], ws, dev)[0]
+        out["job"] = {"ranks": ws, "instances": n_inst, "ms_per_batch_max_over_ranks": med_all,
+                      "instances_per_s": n_inst * 1e3 / med_all, "scaling": "strong (fixed 256-instance batch)"}
     ctx.close()
     return out
 

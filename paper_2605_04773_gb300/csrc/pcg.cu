@@ -68,6 +68,12 @@ struct PcgArgs {
     uint32_t *status;
 };
 
+// FP64 class test on the bit pattern (integer instructions only).
+__device__ __forceinline__ bool finite_bits(double v)
+{
+    return ((__double_as_longlong(v) >> 52) & 0x7ff) != 0x7ff;
+}
+
 // Row-local update of one row i: p = u + beta p, s = w + beta s,
 // x += alpha p, r -= alpha s, u = M^-1 r; returns gamma, rho shares.
 __device__ __forceinline__ void row_update(int64_t i, const double uu[3], const double ww[3], double pp[3], double ss[3],
@@ -246,7 +252,8 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_kernel(PcgArgs A)
     if (ok && gwarp < nslices) issue_slice(wbuf, gwarp, nnz, A.val, A.col, brow, lane);
     cp_async_commit();
 
-    double alpha_old = 1.0, gamma_old = 1.0, bnorm2 = 0.0, rnorm2 = 0.0;
+    double gamma_old = 1.0, bnorm2 = 0.0, rnorm2 = 0.0, tolb = 0.0;
+    double tt = 1.0, ttg = 1.0;   // gamma_old alpha_old and its product with gamma_old
     const double tol2 = A.tol * A.tol;
     int32_t it = 0;
     bool converged = false;
@@ -348,40 +355,50 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_kernel(PcgArgs A)
             // ||r|| <= tol ||b|| is done on squares; alpha needs one division:
             // g / (dl - beta g / alpha_old) with beta = g / gamma_old equals
             // g t / (dl t - g^2), t = gamma_old alpha_old.
+            // The class tests and the range test read the exponent bits
+            // (integer instructions): on this part every FP64 instruction,
+            // compares included, is a long step of the dependent chain.
             int decision = 0;
             double alpha = 0.0, beta = 0.0;
             rnorm2 = rh;
-            if (it == 0) bnorm2 = bb;
-            if (!isfinite(rh) || !isfinite(g) || !isfinite(dl)) decision = 3;
-            else if (bnorm2 == 0.0 || rh <= tol2 * bnorm2) decision = 1;
+            if (it == 0) {
+                bnorm2 = bb;
+                tolb = tol2 * bnorm2;
+            }
+            if (!finite_bits(rh) || !finite_bits(g) || !finite_bits(dl)) decision = 3;
+            else if (bnorm2 == 0.0 || rh <= tolb) decision = 1;
             else if (it >= A.max_iter) decision = 2;
             else {
                 if (it == 0) {
                     alpha = g / dl;
                 } else {
-                    // beta = g / gamma_old and alpha = g t / den share one
-                    // division by gamma_old den (an FP64 division is a long
-                    // dependent chain here); the two quotients are used when
-                    // that product leaves the normal range
-                    const double t = gamma_old * alpha_old;
-                    const double den = fma(dl, t, -g * g);
+                    // beta = g / gamma_old and alpha = g t / den (t carried as
+                    // tt, t gamma_old as ttg) share one division by gamma_old
+                    // den (an FP64 division is a long dependent chain here);
+                    // the two quotients are used when that product leaves the
+                    // normal range
+                    const double den = fma(dl, tt, -g * g);
                     const double q = gamma_old * den;
-                    if (fabs(q) >= 2.2250738585072014e-308 && fabs(q) <= 1.0e300) {
-                        const double inv = 1.0 / q;
-                        beta = g * den * inv;
-                        alpha = g * t * gamma_old * inv;
+                    const int eq = (int)((__double_as_longlong(q) >> 52) & 0x7ff);
+                    if (eq >= 1 && eq <= 2019) {
+                        const double gi = g * (1.0 / q);
+                        beta = gi * den;
+                        alpha = gi * ttg;
                     } else {
                         beta = g / gamma_old;
-                        alpha = (g * t) / den;
+                        alpha = (g * tt) / den;
                     }
                 }
-                if (!isfinite(alpha) || !isfinite(beta)) decision = 3;
-                gamma_old = g;
-                alpha_old = alpha;
+                if (!finite_bits(alpha) || !finite_bits(beta)) decision = 3;
             }
             s_scal[0] = alpha;
             s_scal[1] = beta;
             s_dec = decision;
+            if (decision == 0) {   // after publishing: the next iteration's products
+                gamma_old = g;
+                tt = g * alpha;
+                ttg = tt * g;
+            }
         }
         __syncthreads();
         const double alpha = s_scal[0], beta = s_scal[1];

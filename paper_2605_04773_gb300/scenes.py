@@ -677,9 +677,30 @@ class Batch:
                      meta=dict(instance=i))
 
 
+def _instance_dims(seed: int, i: int, v_range):
+    """Hex-grid cells per axis of instance i (its stream's first draws) and
+    the stream, positioned after them."""
+    rng = np.random.default_rng([seed, i])
+    nv = float(np.exp(rng.uniform(np.log(v_range[0]), np.log(v_range[1]))))
+    rx, ry = np.exp(rng.uniform(-0.7, 0.7, size=2))
+    t = (nv / (rx * ry)) ** (1.0 / 3.0)
+    nx, ny, nz = (max(2, int(round(r * t)) - 1) for r in (rx, ry, 1.0))
+    return (nx, ny, nz), rng
+
+
+def instance_vertex_counts(seed: int = 1004, n_inst: int = 256, v_range=(2000, 60000), first: int = 0):
+    """Vertex counts of instances first .. first + n_inst - 1 of the batched
+    workload, without building their meshes."""
+    out = []
+    for i in range(first, first + n_inst):
+        (nx, ny, nz), _ = _instance_dims(seed, i, v_range)
+        out.append((nx + 1) * (ny + 1) * (nz + 1))
+    return np.asarray(out, dtype=np.int64)
+
+
 def batch_instances(seed: int = 1004, n_inst: int = 256, v_range=(2000, 60000), frac_range=(0.3, 0.9),
                     pair_frac_range=(0.0, 0.05), cell: float = 0.01, E: float = 1e5, nu: float = 0.4,
-                    with_values=False) -> Batch:
+                    with_values=False, first: int = 0) -> Batch:
     """The batched workload: n_inst hex-grid bodies split into Kuhn tets,
     vertex counts log-uniform in v_range, random aspect ratios (each axis
     ratio e^U(-0.7, 0.7)), a collapsible fraction U(frac_range) per instance,
@@ -688,18 +709,17 @@ def batch_instances(seed: int = 1004, n_inst: int = 256, v_range=(2000, 60000), 
     with_values (True, or a collection of instance indices) also sums the
     fine system in numpy for those instances (val, g; NaN elsewhere): small
     batches, or the instances a check samples.  The rest get their values on
-    the GPU from the same physics."""
+    the GPU from the same physics.  first > 0 builds instances first ..
+    first + n_inst - 1 of the same workload (each instance has its own random
+    stream), the contiguous range one rank takes when the batch is sharded.
+    with_values indices are the instances' indices in the whole batch."""
     rho, h, dhat = 1000.0, 1.0 / 60.0, 1e-3
     vptr, tptr, dims, fracs = [0], [0], [], []
     parts = {k: [] for k in ("edges", "tags", "row_ptr", "col", "tets", "X", "x", "mass", "pidx", "pblk", "pgrad",
                              "val", "g")}
     nnz_off = 0
-    for i in range(n_inst):
-        rng = np.random.default_rng([seed, i])
-        nv = float(np.exp(rng.uniform(np.log(v_range[0]), np.log(v_range[1]))))
-        rx, ry = np.exp(rng.uniform(-0.7, 0.7, size=2))
-        t = (nv / (rx * ry)) ** (1.0 / 3.0)
-        nx, ny, nz = (max(2, int(round(r * t)) - 1) for r in (rx, ry, 1.0))
+    for i in range(first, first + n_inst):
+        (nx, ny, nz), rng = _instance_dims(seed, i, v_range)
         frac = float(rng.uniform(*frac_range))
         X, tets = kuhn_hex_grid(nx, ny, nz, cell)
         edges, row_ptr, col = kuhn_structure(nx, ny, nz)
