@@ -419,20 +419,37 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_kernel(PcgArgs A)
             if (has_row) row_update(my_row, ru, rw, rp_, rs, rr_, rx, rD, alpha, beta, p, s, r, x, u, w,
                                     rowflag[my_row] != 0, gpart, rpart);
         } else {
-            for (int64_t i = row0 + threadIdx.x; i < row1; i += blockDim.x) {
-                double uu[3], ww[3], pp[3], ss[3], rr[3], xx[3], D[9];
+            // kRows rows per thread per pass: every load of the pass is
+            // issued before the first store, so their latencies overlap
+            constexpr int kRows = 2;
+            for (int64_t i0 = row0 + threadIdx.x; i0 < row1; i0 += kRows * (int64_t)blockDim.x) {
+                double uu[kRows][3], ww[kRows][3], pp[kRows][3], ss[kRows][3], rr[kRows][3], xx[kRows][3];
+                double D[kRows][9];
+                bool fl[kRows];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    uu[c] = __ldcg(u + 3 * i + c);
-                    ww[c] = __ldcg(w + 3 * i + c);
-                    pp[c] = p[3 * i + c];
-                    ss[c] = s[3 * i + c];
-                    rr[c] = r[3 * i + c];
-                    xx[c] = x[3 * i + c];
+                for (int j = 0; j < kRows; ++j) {
+                    const int64_t i = i0 + j * (int64_t)blockDim.x;
+                    const int64_t k = i < row1 ? i : i0;   // a row of this pass that exists
+                    fl[j] = rowflag[k] != 0;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        uu[j][c] = __ldcg(u + 3 * k + c);
+                        ww[j][c] = __ldcg(w + 3 * k + c);
+                        pp[j][c] = p[3 * k + c];
+                        ss[j][c] = s[3 * k + c];
+                        rr[j][c] = r[3 * k + c];
+                        xx[j][c] = x[3 * k + c];
+                    }
+#pragma unroll
+                    for (int e = 0; e < 9; ++e) D[j][e] = A.dinv[9 * k + e];
                 }
 #pragma unroll
-                for (int e = 0; e < 9; ++e) D[e] = A.dinv[9 * i + e];
-                row_update(i, uu, ww, pp, ss, rr, xx, D, alpha, beta, p, s, r, x, u, w, rowflag[i] != 0, gpart, rpart);
+                for (int j = 0; j < kRows; ++j) {
+                    const int64_t i = i0 + j * (int64_t)blockDim.x;
+                    if (i >= row1) break;
+                    row_update(i, uu[j], ww[j], pp[j], ss[j], rr[j], xx[j], D[j], alpha, beta, p, s, r, x, u, w,
+                               fl[j], gpart, rpart);
+                }
             }
         }
         s_gr[2 * threadIdx.x] = gpart;

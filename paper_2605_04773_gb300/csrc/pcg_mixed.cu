@@ -59,11 +59,13 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_mixed_kernel(MixedArgs A)
     __shared__ double s_gr[2 * kPcgBlock];   // the P phase's per-thread gamma, rho shares
     __shared__ int s_dec;
     __shared__ bool s_ref;
+    __shared__ int s_abort;
+    __shared__ __align__(8) uint64_t s_mbar[kPcgWarps * 3];   // one per ring slot of each warp
 
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const unsigned nblocks = gridDim.x;
     const int64_t nwarps = (int64_t)nblocks * kPcgWarps;
-    const int64_t gwarp = (int64_t)wib * nblocks + blockIdx.x;
+    const int64_t gwarp = (int64_t)wib * nblocks + blockIdx.x;  // slices interleave over CTAs
     const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
 
     const int32_t n = *A.n_dev;
@@ -82,14 +84,16 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_mixed_kernel(MixedArgs A)
     const int64_t row0 = min64((int64_t)blockIdx.x * rows_per_cta, n);
     const int64_t row1 = min64(row0 + rows_per_cta, n);
 
-    // vectors: r, ax in FP64; u, w, p, s in FP32 (two FP32 vectors share one
-    // FP64-sized scratch array)
+    // vectors: r, ax in FP64; u, w, p, s in FP32.  u is packed 16 bytes per
+    // row, (u_0, u_1, u_2, the row's flag bits), so a slice gathers a column
+    // with one load; it fills 4 of the 6 FP32 words per row of an FP64-sized
+    // scratch array, and w shares s's array (3 + 3 words per row).
     double *__restrict__ r = A.S.r;
     double *ax = A.S.u;
-    float *w = reinterpret_cast<float *>(A.S.w);
-    float *u = w + 3 * (int64_t)A.max_rows;
+    float4 *u4 = reinterpret_cast<float4 *>(A.S.w);
     float *__restrict__ p = reinterpret_cast<float *>(A.S.p);
     float *__restrict__ s = reinterpret_cast<float *>(A.S.s);
+    float *w = s + 3 * (int64_t)A.max_rows;
     double *__restrict__ x = A.x;
     int32_t *brow = A.S.brow;
     uint8_t *rowflag = A.S.rowflag;
@@ -130,9 +134,9 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_mixed_kernel(MixedArgs A)
             r[3 * i + c] = rr[c];
         }
         precond32(A.dinv32 + 9 * i, rr, uu);
+        u4[i] = make_float4(uu[0], uu[1], uu[2], __int_as_float((int)f));
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            u[3 * i + c] = uu[c];
             gpart = fma(rr[c], (double)uu[c], gpart);
             rpart = fma(rr[c], rr[c], rpart);
         }
@@ -150,9 +154,69 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_mixed_kernel(MixedArgs A)
         if (gtid == 0) set_status(A.status, ST_BAD_INDEX);
         ok = false;
     }
-    int nb = 0;
-    if (ok && gwarp < nslices) issue_slice(wbuf, gwarp, nnz, A.val32, A.col, brow, lane);
-    cp_async_commit();
+    // Resident mode: the warp's one FP32 slice stays in buffer 0 and the FP64
+    // slice of a residual replacement goes to the region after it.  Streamed
+    // mode (the matrix does not fit in shared memory): the warp cycles its
+    // slices through a ring of kRing FP32 buffers, kRing - 1 of them loading
+    // while it multiplies with another; the first kRing - 1 slices of an S
+    // phase are issued at the end of the previous iteration, so they load
+    // during the grid barrier.  The FP64 slices of a residual replacement
+    // double-buffer over the ring's region.
+    constexpr int kRing = 3;
+    constexpr int kB32 = SliceLayout<float>::kBuf;
+    constexpr int kB64 = SliceLayout<double>::kBuf;
+    static_assert(kRing * kB32 <= 2 * kBufBytes && kB32 + kB64 <= 2 * kBufBytes && 2 * kB64 <= 2 * kBufBytes &&
+                      kB32 % 16 == 0 && kB64 % 16 == 0,
+                  "slice buffers overflow the warp's region");
+    // A full slice goes by TMA bulk copy and completes on its slot's
+    // mbarrier; the ragged last slice of the matrix goes by the zero-filling
+    // cp.async path (a bulk copy would need lengths rounded up to 16 bytes,
+    // past the caller's arrays).  `ph` holds each slot's next parity, `pend`
+    // the slots with a bulk copy in flight (drained before the kernel ends).
+    static_assert(kRing == 3, "one mbarrier per ring slot");
+    uint64_t *mbar = s_mbar + kRing * wib;
+    unsigned ph = 0, pend = 0;
+    if (threadIdx.x == 0) s_abort = 0;
+    if (lane == 0)
+        for (int k = 0; k < kRing; ++k) mbar_init(mbar + k);
+    __syncthreads();
+    auto ring_issue = [&](int k, int64_t sl) {
+        if ((sl + 1) * kSlice <= nnz) {
+            issue_slice_bulk<float>(wbuf + k * kB32, sl, A.val32, A.col, brow, mbar + k, lane);
+            pend |= 1u << k;
+        } else {
+            issue_slice(wbuf + k * kB32, sl, nnz, A.val32, A.col, brow, lane);
+            cp_async_commit();
+        }
+    };
+    auto ring_wait = [&](int k, int64_t sl) {
+        if ((sl + 1) * kSlice <= nnz) {
+            if (!mbar_wait(mbar + k, (ph >> k) & 1u)) {
+                set_status(A.status, ST_TIMEOUT);
+                s_abort = 1;
+            }
+            ph ^= 1u << k;
+            pend &= ~(1u << k);
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncwarp();
+    };
+    auto prefetch_ring = [&]() {
+#pragma unroll
+        for (int k = 0; k < kRing - 1; ++k) {
+            const int64_t sl = gwarp + k * nwarps;
+            if (sl < nslices) ring_issue(k, sl);
+        }
+    };
+    if (ok) {
+        if (!resident) {
+            prefetch_ring();
+        } else {
+            if (gwarp < nslices) issue_slice(wbuf, gwarp, nnz, A.val32, A.col, brow, lane);
+            cp_async_commit();
+        }
+    }
 
     double alpha_old = 1.0, gamma_old = 1.0, bnorm2 = 0.0, rnorm2 = 0.0;
     const double tol2 = A.tol * A.tol;
@@ -166,19 +230,46 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_mixed_kernel(MixedArgs A)
         double *part = partials + par * pstride;
         // ---- S phase: w = A32 u (FP32), delta accumulated in FP64 per lane
         double dpart = 0.0;
-        for (int64_t sl = gwarp; sl < nslices; sl += nwarps) {
-            if (!resident) {
-                const int64_t next = sl + nwarps < nslices ? sl + nwarps : gwarp;
-                issue_slice(wbuf + (nb ^ 1) * kBufBytes, next, nnz, A.val32, A.col, brow, lane);
-                cp_async_commit();
-                cp_async_wait<1>();
-            } else {
+        if (resident) {
+            if (gwarp < nslices) {
                 cp_async_wait<0>();
+                __syncwarp();
+                const int cnt = (int)min64(kSlice, nnz - gwarp * kSlice);
+                SliceGather<float> G;
+                slice_gather_packed(wbuf, cnt, u4, lane, G);
+                slice_compute<float, true>(wbuf, G, w, join, lane, dpart);
             }
-            __syncwarp();
-            const int cnt = (int)min64(kSlice, nnz - sl * kSlice);
-            slice_spmv<float, true>(wbuf + nb * kBufBytes, cnt, u, w, rowflag, join, lane, dpart);
-            if (!resident) nb ^= 1;
+        } else {
+            // The k-th slice of the warp sits in ring slot k mod kRing.  While
+            // slice k is multiplied, the gathers of slice k + 1 (landed) are in
+            // flight and slice k + 2 loads into the slot slice k - 1 used.
+            // Two gather sets alternate (no copies between them, which would
+            // wait for the loads in flight).
+            static_assert(kRing == 3, "the gather pipeline holds three slices");
+            SliceGather<float> G0, G1;
+            int slot = 0;
+            if (gwarp < nslices) {
+                ring_wait(0, gwarp);          // the first prefetched slice
+                slice_gather_packed(wbuf, (int)min64(kSlice, nnz - gwarp * kSlice), u4, lane, G0);
+            }
+            // one step: refill the slot slice k - 1 used with slice k + 2,
+            // gather slice k + 1 into Gn, multiply slice k with Gc
+            auto step = [&](int64_t sl, SliceGather<float> &Gc, SliceGather<float> &Gn) {
+                const int64_t ahead = sl + (kRing - 1) * nwarps;
+                if (ahead < nslices) ring_issue(slot == 0 ? kRing - 1 : slot - 1, ahead);
+                const int nslot = slot == kRing - 1 ? 0 : slot + 1;
+                const int64_t nx = sl + nwarps;
+                if (nx < nslices) {
+                    ring_wait(nslot, nx);     // slice k + 1 (slice k + 2 may still load)
+                    slice_gather_packed(wbuf + nslot * kB32, (int)min64(kSlice, nnz - nx * kSlice), u4, lane, Gn);
+                }
+                slice_compute<float, true>(wbuf + slot * kB32, Gc, w, join, lane, dpart);
+                slot = nslot;
+            };
+            for (int64_t sl = gwarp; sl < nslices; sl += 2 * nwarps) {
+                step(sl, G0, G1);
+                if (sl + nwarps < nslices) step(sl + nwarps, G1, G0);
+            }
         }
         if (pending && wib == kPcgWarps - 1) {
             // the previous P phase's gamma and rho shares, summed over the CTA
@@ -207,6 +298,7 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_mixed_kernel(MixedArgs A)
             cta_sum<1>(v, s_part, s_tot);
             if (threadIdx.x == 0) part[2 * mg + blockIdx.x] = v[0];
         }
+        if (s_abort) { ok = false; break; }   // a slice never arrived (ST_TIMEOUT is set)
         if (!grid_sync(count, nblocks, epoch, A.status)) { ok = false; break; }
 
         // ---- global scalars (as in the FP64 kernel)
@@ -303,11 +395,9 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_mixed_kernel(MixedArgs A)
         // them to that slot.
         gpart = 0.0;
         rpart = 0.0;
-        for (int64_t i = row0 + threadIdx.x; i < row1; i += blockDim.x) {
-            double rr[3];
-            float pp[3], ss[3];
-            if (verify) {
-                // no Krylov step: only clear the rows that receive atomics
+        if (verify) {
+            // no Krylov step: only clear the rows that receive atomics
+            for (int64_t i = row0 + threadIdx.x; i < row1; i += blockDim.x)
                 if (rowflag[i]) {
                     w[3 * i] = 0.0f;
                     w[3 * i + 1] = 0.0f;
@@ -316,37 +406,71 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_mixed_kernel(MixedArgs A)
                     ax[3 * i + 1] = 0.0;
                     ax[3 * i + 2] = 0.0;
                 }
-                continue;
-            }
+        } else {
+            // kRows rows per thread per pass: every load of the pass is issued
+            // before the first store, so their latencies overlap
+            constexpr int kRows = 2;
+            for (int64_t i0 = row0 + threadIdx.x; i0 < row1; i0 += kRows * (int64_t)blockDim.x) {
+                float uu[kRows][3], ww[kRows][3], pp[kRows][3], ss[kRows][3], D[kRows][9];
+                double xx[kRows][3], rr[kRows][3];
+                uint8_t fl[kRows];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float uu = __ldcg(u + 3 * i + c), ww = __ldcg(w + 3 * i + c);
-                pp[c] = fmaf(beta32, p[3 * i + c], uu);
-                ss[c] = fmaf(beta32, s[3 * i + c], ww);
-                p[3 * i + c] = pp[c];
-                s[3 * i + c] = ss[c];
-                x[3 * i + c] = fma(alpha, (double)pp[c], x[3 * i + c]);
-                rr[c] = fma(-alpha, (double)ss[c], r[3 * i + c]);
-                r[3 * i + c] = rr[c];
-            }
-            if (rowflag[i]) {
-                w[3 * i] = 0.0f;
-                w[3 * i + 1] = 0.0f;
-                w[3 * i + 2] = 0.0f;
-                if (refine) {
-                    ax[3 * i] = 0.0;
-                    ax[3 * i + 1] = 0.0;
-                    ax[3 * i + 2] = 0.0;
+                for (int j = 0; j < kRows; ++j) {
+                    const int64_t i = i0 + j * (int64_t)blockDim.x;
+                    const bool has = i < row1;
+                    const int64_t k = has ? i : i0;   // a row of this pass that exists
+                    fl[j] = has ? rowflag[k] : 0;
+                    const float4 u_k = __ldcg(u4 + k);
+                    uu[j][0] = u_k.x;
+                    uu[j][1] = u_k.y;
+                    uu[j][2] = u_k.z;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        ww[j][c] = __ldcg(w + 3 * k + c);
+                        pp[j][c] = p[3 * k + c];
+                        ss[j][c] = s[3 * k + c];
+                        xx[j][c] = x[3 * k + c];
+                        rr[j][c] = r[3 * k + c];
+                    }
+                    if (!refine) {
+#pragma unroll
+                        for (int e = 0; e < 9; ++e) D[j][e] = A.dinv32[9 * k + e];
+                    }
                 }
-            }
-            if (!refine) {
-                float uu[3];
-                precond32(A.dinv32 + 9 * i, rr, uu);
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    u[3 * i + c] = uu[c];
-                    gpart = fma(rr[c], (double)uu[c], gpart);
-                    rpart = fma(rr[c], rr[c], rpart);
+                for (int j = 0; j < kRows; ++j) {
+                    const int64_t i = i0 + j * (int64_t)blockDim.x;
+                    if (i >= row1) break;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        pp[j][c] = fmaf(beta32, pp[j][c], uu[j][c]);
+                        ss[j][c] = fmaf(beta32, ss[j][c], ww[j][c]);
+                        p[3 * i + c] = pp[j][c];
+                        s[3 * i + c] = ss[j][c];
+                        x[3 * i + c] = fma(alpha, (double)pp[j][c], xx[j][c]);
+                        rr[j][c] = fma(-alpha, (double)ss[j][c], rr[j][c]);
+                        r[3 * i + c] = rr[j][c];
+                    }
+                    if (fl[j]) {
+                        w[3 * i] = 0.0f;
+                        w[3 * i + 1] = 0.0f;
+                        w[3 * i + 2] = 0.0f;
+                        if (refine) {
+                            ax[3 * i] = 0.0;
+                            ax[3 * i + 1] = 0.0;
+                            ax[3 * i + 2] = 0.0;
+                        }
+                    }
+                    if (!refine) {
+                        float un[3];
+                        precond32(D[j], rr[j], un);
+                        u4[i] = make_float4(un[0], un[1], un[2], __int_as_float((int)fl[j]));
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            gpart = fma(rr[j][c], (double)un[c], gpart);
+                            rpart = fma(rr[j][c], rr[j][c], rpart);
+                        }
+                    }
                 }
             }
         }
@@ -354,14 +478,32 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_mixed_kernel(MixedArgs A)
             // ---- residual replacement: r = b - A64 x with the FP64 master matrix
             if (!grid_sync(count, nblocks, epoch, A.status)) { ok = false; break; }
             double dummy = 0.0;
-            for (int64_t sl = gwarp; sl < nslices; sl += nwarps) {
-                unsigned char *fb = wbuf + (nb ^ 1) * kBufBytes;
-                issue_slice(fb, sl, nnz, A.val64, A.col, brow, lane);
+            if (resident) {
+                unsigned char *fb = wbuf + kB32;
+                if (gwarp < nslices) {
+                    issue_slice(fb, gwarp, nnz, A.val64, A.col, brow, lane);
+                    cp_async_commit();
+                    cp_async_wait<0>();
+                    __syncwarp();
+                    const int cnt = (int)min64(kSlice, nnz - gwarp * kSlice);
+                    slice_spmv<double, false>(fb, cnt, x, ax, rowflag, join, lane, dummy);
+                }
+            } else {
+                // the ring is empty here (the next S phase's slices are issued
+                // after this pass)
+                int fbi = 0;
+                if (gwarp < nslices) issue_slice(wbuf, gwarp, nnz, A.val64, A.col, brow, lane);
                 cp_async_commit();
-                cp_async_wait<0>();
-                __syncwarp();
-                const int cnt = (int)min64(kSlice, nnz - sl * kSlice);
-                slice_spmv<double, false>(fb, cnt, x, ax, rowflag, join, lane, dummy);
+                for (int64_t sl = gwarp; sl < nslices; sl += nwarps) {
+                    const int64_t next = sl + nwarps;
+                    if (next < nslices) issue_slice(wbuf + (fbi ^ 1) * kB64, next, nnz, A.val64, A.col, brow, lane);
+                    cp_async_commit();
+                    cp_async_wait<1>();
+                    __syncwarp();
+                    const int cnt = (int)min64(kSlice, nnz - sl * kSlice);
+                    slice_spmv<double, false>(wbuf + fbi * kB64, cnt, x, ax, rowflag, join, lane, dummy);
+                    fbi ^= 1;
+                }
             }
             if (!grid_sync(count, nblocks, epoch, A.status)) { ok = false; break; }
             for (int64_t i = row0 + threadIdx.x; i < row1; i += blockDim.x) {
@@ -373,9 +515,9 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_mixed_kernel(MixedArgs A)
                     r[3 * i + c] = rr[c];
                 }
                 precond32(A.dinv32 + 9 * i, rr, uu);
+                u4[i] = make_float4(uu[0], uu[1], uu[2], __int_as_float((int)rowflag[i]));
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    u[3 * i + c] = uu[c];
                     gpart = fma(rr[c], (double)uu[c], gpart);
                     rpart = fma(rr[c], rr[c], rpart);
                 }
@@ -385,8 +527,12 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_mixed_kernel(MixedArgs A)
         s_gr[2 * threadIdx.x + 1] = rpart;
         pending = true;
         if (!verify) ++it;
+        if (!resident) prefetch_ring();
         if (!grid_sync(count, nblocks, epoch, A.status)) { ok = false; break; }
     }
+    // no copy into this CTA's shared memory may outlive it
+    for (int k = 0; k < kRing; ++k)
+        if ((pend >> k) & 1u) mbar_wait(mbar + k, (ph >> k) & 1u);
     cp_async_wait<0>();
     if (gtid == 0 && (ok || it > 0)) {
         *A.iters_dev = it;

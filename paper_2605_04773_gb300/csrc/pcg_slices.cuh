@@ -15,8 +15,16 @@ constexpr int kK = 4;                          // consecutive blocks per lane
 // the SM sub-partitions; 6.5 % less time per coarse iteration on GB300)
 constexpr int kSlice = 32 * kK;                // blocks per warp slice
 constexpr int kValBytes = kSlice * 9 * 8;      // 9216
-constexpr int kIdxBytes = kSlice * 4;          // 640 per index array
+constexpr int kIdxBytes = kSlice * 4;          // 512 per index array
 constexpr int kBufBytes = kValBytes + 2 * kIdxBytes;
+// A slice buffer holds the values (9 per block, of type T), then the column
+// and the row of every block.  FP32 slices take 5632 bytes, so three of them
+// fit where two FP64 slices go.
+template <class T>
+struct SliceLayout {
+    static constexpr int kVal = kSlice * 9 * (int)sizeof(T);
+    static constexpr int kBuf = kVal + 2 * kIdxBytes;
+};
 constexpr int kJoinBytes = 32 * (3 * 8 + 3 * 4);
 constexpr int kWarpSmem = 2 * kBufBytes + kJoinBytes;
 constexpr int kPartBytes = kPcgBlock * 3 * 8;
@@ -34,6 +42,60 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+// ---- TMA bulk copies of whole slices, completing on a shared-memory
+// mbarrier (one per ring slot).  A full slice is three 16-byte-aligned runs
+// (values, columns, rows) whose lengths are multiples of 16 bytes; one lane
+// issues them.  Waits poll mbarrier.test_wait (which returns at once) and
+// give up after kSpinLimit polls.
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+template <class T>
+__device__ __forceinline__ void issue_slice_bulk(unsigned char *buf, int64_t sl, const T *val, const int32_t *col,
+                                                 const int32_t *brow, uint64_t *bar, int lane)
+{
+    if (lane != 0) return;
+    constexpr unsigned kV = SliceLayout<T>::kVal, kI = kIdxBytes;
+    const unsigned b = smem_u32(bar), d = smem_u32(buf);
+    // the warp's earlier reads of this buffer (generic proxy) come before
+    // the copy's writes (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(kV + 2 * kI) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(d),
+                 "l"(val + 9 * sl * kSlice), "r"(kV), "r"(b)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     d + kV),
+                 "l"(col + sl * kSlice), "r"(kI), "r"(b)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     d + kV + kI),
+                 "l"(brow + sl * kSlice), "r"(kI), "r"(b)
+                 : "memory");
+}
+
+// Waits (every lane) for the phase of parity `parity` of `bar` to complete;
+// false after kSpinLimit polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
+{
+    const unsigned b = smem_u32(bar);
+    for (long long spins = 0; spins < kSpinLimit; ++spins) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(b), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 // Copy slice `sl` (values, columns, rows) into a warp buffer; zero-fills
 // past the last block so no byte beyond the arrays is read.
 template <class T>
@@ -48,8 +110,8 @@ __device__ __forceinline__ void issue_slice(unsigned char *buf, int64_t sl, int6
     const unsigned char *rs = reinterpret_cast<const unsigned char *>(brow + base);
     for (int q = lane; 16 * q < vbytes; q += 32) cp_async16(buf + 16 * q, vs + 16 * q, min(16, vbytes - 16 * q));
     for (int q = lane; 16 * q < ibytes; q += 32) {
-        cp_async16(buf + kValBytes + 16 * q, cs + 16 * q, min(16, ibytes - 16 * q));
-        cp_async16(buf + kValBytes + kIdxBytes + 16 * q, rs + 16 * q, min(16, ibytes - 16 * q));
+        cp_async16(buf + SliceLayout<T>::kVal + 16 * q, cs + 16 * q, min(16, ibytes - 16 * q));
+        cp_async16(buf + SliceLayout<T>::kVal + kIdxBytes + 16 * q, rs + 16 * q, min(16, ibytes - 16 * q));
     }
 }
 
@@ -191,10 +253,124 @@ __device__ __forceinline__ void join_rows(int lane, int fr, T (&fa)[3], bool f_s
     __syncwarp();
 }
 
+// A lane's kK blocks take 9 kK sizeof(T) bytes (144 in FP32, 288 in FP64)
+// and every slice buffer starts on a 16-byte boundary, so each 144-byte
+// chunk of a lane (4 FP32 or 2 FP64 blocks) is read with nine 16-byte
+// shared loads: conflict-free at this lane stride, where scalar loads met
+// 4-way bank conflicts.
+__device__ __forceinline__ void load_chunk(const float *src, float (&v)[36])
+{
+    const float4 *s4 = reinterpret_cast<const float4 *>(src);
+#pragma unroll
+    for (int m = 0; m < 9; ++m) {
+        const float4 t = s4[m];
+        v[4 * m] = t.x;
+        v[4 * m + 1] = t.y;
+        v[4 * m + 2] = t.z;
+        v[4 * m + 3] = t.w;
+    }
+}
+__device__ __forceinline__ void load_chunk(const double *src, double (&v)[18])
+{
+    const double2 *s2 = reinterpret_cast<const double2 *>(src);
+#pragma unroll
+    for (int m = 0; m < 9; ++m) {
+        const double2 t = s2[m];
+        v[2 * m] = t.x;
+        v[2 * m + 1] = t.y;
+    }
+}
+
+// What a lane gathers from global memory for its kK blocks of a slice: the
+// rows, u at the columns, u at the row of each segment's first block and the
+// row's flag word (bit 0: the row is split).  Issued by slice_gather,
+// consumed by slice_compute, so a streamed loop can gather slice k + 1 while
+// it multiplies slice k: the gather step only issues loads and never uses a
+// loaded value (the flag's bit is tested in slice_compute).
+//
+// The gathers are plain (L1-cacheable) loads: the rows of a slice share most
+// of their neighbour columns, and routed past L1 every component became its
+// own L2 sector request, which bounded the streamed SpMV.  u and the flags
+// are written only in other phases, each followed by a grid barrier whose
+// acquire orders those writes before these loads (PTX memory model), so no
+// L1 line read here can predate them.
+template <class T>
+struct SliceGather {
+    int rows_[kK];
+    T xv[kK][3];
+    T ur[kK][3];
+    int flags[kK];
+};
+
+template <class T>
+__device__ __forceinline__ void slice_gather(const unsigned char *buf, int cnt, const T *u, const uint8_t *rowflag,
+                                             int lane, SliceGather<T> &G)
+{
+    const int32_t *s_col = reinterpret_cast<const int32_t *>(buf + SliceLayout<T>::kVal);
+    const int32_t *s_row = reinterpret_cast<const int32_t *>(buf + SliceLayout<T>::kVal + kIdxBytes);
+#pragma unroll
+    for (int j = 0; j < kK; ++j) {
+        const int q = lane * kK + j;
+        G.rows_[j] = -1;
+        G.flags[j] = 0;
+        G.xv[j][0] = G.xv[j][1] = G.xv[j][2] = T(0);
+        G.ur[j][0] = G.ur[j][1] = G.ur[j][2] = T(0);
+        if (q < cnt) {
+            const int rj = s_row[q];
+            G.rows_[j] = rj;
+            const T *uc = u + 3 * (int64_t)s_col[q];
+            G.xv[j][0] = uc[0];
+            G.xv[j][1] = uc[1];
+            G.xv[j][2] = uc[2];
+            if (j == 0 || rj != s_row[q - 1]) {  // first block of a row segment
+                const T *up = u + 3 * (int64_t)rj;
+                G.ur[j][0] = up[0];
+                G.ur[j][1] = up[1];
+                G.ur[j][2] = up[2];
+                G.flags[j] = rowflag[rj];
+            }
+        }
+    }
+}
+
+// The same gathers from a packed FP32 vector: row i at u4[i] = (u_0, u_1,
+// u_2, the row's flag bits), so a column costs one 16-byte load and the
+// split flag rides with u of the segment's row.
+__device__ __forceinline__ void slice_gather_packed(const unsigned char *buf, int cnt, const float4 *u4, int lane,
+                                                    SliceGather<float> &G)
+{
+    const int32_t *s_col = reinterpret_cast<const int32_t *>(buf + SliceLayout<float>::kVal);
+    const int32_t *s_row = reinterpret_cast<const int32_t *>(buf + SliceLayout<float>::kVal + kIdxBytes);
+#pragma unroll
+    for (int j = 0; j < kK; ++j) {
+        const int q = lane * kK + j;
+        G.rows_[j] = -1;
+        G.flags[j] = 0;
+        G.xv[j][0] = G.xv[j][1] = G.xv[j][2] = 0.0f;
+        G.ur[j][0] = G.ur[j][1] = G.ur[j][2] = 0.0f;
+        if (q < cnt) {
+            const int rj = s_row[q];
+            G.rows_[j] = rj;
+            const float4 c4 = u4[s_col[q]];
+            G.xv[j][0] = c4.x;
+            G.xv[j][1] = c4.y;
+            G.xv[j][2] = c4.z;
+            if (j == 0 || rj != s_row[q - 1]) {  // first block of a row segment
+                const float4 r4 = u4[rj];
+                G.ur[j][0] = r4.x;
+                G.ur[j][1] = r4.y;
+                G.ur[j][2] = r4.z;
+                G.flags[j] = __float_as_int(r4.w);
+            }
+        }
+    }
+}
+
 // w = A u over one slice held in `buf` (rows inside the slice) or += (rows
-// cut by its ends); with kDelta, adds this lane's share of delta = u . A u
-// (accumulated in T over the lane's row segments) to dpart.  T is the type
-// of the matrix values, of u and w and of the accumulation.
+// cut by its ends), with the lane's gathers in G; with kDelta, adds this
+// lane's share of delta = u . A u (accumulated in T over the lane's row
+// segments) to dpart.  T is the type of the matrix values, of u and w and
+// of the accumulation.
 //
 // Per lane the kK blocks are folded left to right into one running row
 // accumulator (reset at a row change by a select, so the FP64 work is
@@ -206,39 +382,16 @@ __device__ __forceinline__ void join_rows(int lane, int fr, T (&fa)[3], bool f_s
 // joined by the lane where the row starts, which walks forward over the
 // lanes that continue it.
 template <class T, bool kDelta>
-__device__ __forceinline__ void slice_spmv(const unsigned char *buf, int cnt, const T *u, T *w,
-                                           const uint8_t *rowflag, unsigned char *join, int lane, double &dpart)
+__device__ __forceinline__ void slice_compute(const unsigned char *buf, const SliceGather<T> &G, T *w,
+                                              unsigned char *join, int lane, double &dpart)
 {
     const T *s_val = reinterpret_cast<const T *>(buf);
-    const int32_t *s_col = reinterpret_cast<const int32_t *>(buf + kValBytes);
-    const int32_t *s_row = reinterpret_cast<const int32_t *>(buf + kValBytes + kIdxBytes);
-    int rows_[kK];
-    T xv[kK][3];
-    T ur[kK][3];
+    const int(&rows_)[kK] = G.rows_;
+    const T(&xv)[kK][3] = G.xv;
+    const T(&ur)[kK][3] = G.ur;
     bool split[kK];
 #pragma unroll
-    for (int j = 0; j < kK; ++j) {
-        const int q = lane * kK + j;
-        rows_[j] = -1;
-        split[j] = false;
-        xv[j][0] = xv[j][1] = xv[j][2] = T(0);
-        ur[j][0] = ur[j][1] = ur[j][2] = T(0);
-        if (q < cnt) {
-            const int rj = s_row[q];
-            rows_[j] = rj;
-            const T *uc = u + 3 * (int64_t)s_col[q];
-            xv[j][0] = __ldcg(uc);
-            xv[j][1] = __ldcg(uc + 1);
-            xv[j][2] = __ldcg(uc + 2);
-            if (j == 0 || rj != s_row[q - 1]) {  // first block of a row segment
-                const T *up = u + 3 * (int64_t)rj;
-                ur[j][0] = __ldcg(up);
-                ur[j][1] = __ldcg(up + 1);
-                ur[j][2] = __ldcg(up + 2);
-                split[j] = (__ldcg(rowflag + rj) & 1) != 0;
-            }
-        }
-    }
+    for (int j = 0; j < kK; ++j) split[j] = (G.flags[j] & 1) != 0;
     // running accumulator; segment bookkeeping by selects
     T acc[3] = {T(0), T(0), T(0)};
     T fa[3] = {T(0), T(0), T(0)}, la[3] = {T(0), T(0), T(0)};
@@ -247,6 +400,9 @@ __device__ __forceinline__ void slice_spmv(const unsigned char *buf, int cnt, co
     int fr = -1, lr = -1;
     bool f_split = false, l_split = false, s_cur = false, first_open = true;
     T cu[3] = {T(0), T(0), T(0)};
+    constexpr int kBpc = 16 / (int)sizeof(T);   // blocks per 144-byte chunk
+    static_assert(kK % kBpc == 0, "a lane's blocks are whole chunks");
+    T ch[9 * kBpc];
 #pragma unroll
     for (int j = 0; j < kK; ++j) {
         const bool valid = rows_[j] >= 0;
@@ -254,10 +410,10 @@ __device__ __forceinline__ void slice_spmv(const unsigned char *buf, int cnt, co
         const bool end = valid && (j == kK - 1 || rows_[j + 1] != rows_[j]);
         // blocks past the slice's end read stale shared memory, which may
         // hold NaN bit patterns: select zeros for them (NaN * 0 is NaN)
-        const T *Bs = s_val + 9 * (lane * kK + j);
+        if (j % kBpc == 0) load_chunk(s_val + 9 * (lane * kK + j), ch);
         T B[9];
 #pragma unroll
-        for (int e = 0; e < 9; ++e) B[e] = dsel(valid, Bs[e], T(0));
+        for (int e = 0; e < 9; ++e) B[e] = dsel(valid, ch[9 * (j % kBpc) + e], T(0));
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             cu[c] = dsel(start, ur[j][c], cu[c]);
@@ -289,6 +445,16 @@ __device__ __forceinline__ void slice_spmv(const unsigned char *buf, int cnt, co
         dpart += (double)dloc;
     }
     join_rows(lane, fr, fa, f_split, lr, la, l_split, w, join);
+}
+
+// Gather, then multiply: one slice with nothing overlapped.
+template <class T, bool kDelta>
+__device__ __forceinline__ void slice_spmv(const unsigned char *buf, int cnt, const T *u, T *w,
+                                           const uint8_t *rowflag, unsigned char *join, int lane, double &dpart)
+{
+    SliceGather<T> G;
+    slice_gather<T>(buf, cnt, u, rowflag, lane, G);
+    slice_compute<T, kDelta>(buf, G, w, join, lane, dpart);
 }
 
 }  // namespace pcgs
