@@ -41,7 +41,7 @@ class AgipcError(RuntimeError):
 
 class _PcgOptions(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("rhs_sign", ctypes.c_int32),
-                ("use_x0", ctypes.c_int32)]
+                ("use_x0", ctypes.c_int32), ("streamed", ctypes.c_int32)]
 
 
 def library_path() -> str:
@@ -178,8 +178,8 @@ def agipc_assemble_coarse(ctx: Context, n_fine: int, labels, n_coarse_dev, fine_
 
 
 def agipc_pcg(ctx: Context, max_rows: int, n_rows_dev, row_ptr, col, val, dinv, b, x, tol: float, max_iter: int,
-              rhs_sign: int, iters_dev, relres_dev, use_x0: bool = False):
-    opt = _PcgOptions(float(tol), int(max_iter), int(rhs_sign), 1 if use_x0 else 0)
+              rhs_sign: int, iters_dev, relres_dev, use_x0: bool = False, streamed: bool = False):
+    opt = _PcgOptions(float(tol), int(max_iter), int(rhs_sign), 1 if use_x0 else 0, 1 if streamed else 0)
     _check(load().agipc_pcg(ctx.handle, int(max_rows), _ptr(n_rows_dev), _ptr(row_ptr), _ptr(col), _ptr(val),
                             _ptr(dinv), _ptr(b), _ptr(x), ctypes.byref(opt), _ptr(iters_dev), _ptr(relres_dev)),
            "agipc_pcg")
@@ -209,8 +209,8 @@ def agipc_assemble_coarse_mixed(ctx: Context, n_fine: int, labels, n_coarse_dev,
 
 
 def agipc_pcg_mixed(ctx: Context, max_rows: int, n_rows_dev, row_ptr, col, val, val32, dinv32, b, x, tol: float,
-                    max_iter: int, rhs_sign: int, refine_every: int, iters_dev, relres_dev):
-    opt = _PcgOptions(float(tol), int(max_iter), int(rhs_sign), 0)
+                    max_iter: int, rhs_sign: int, refine_every: int, iters_dev, relres_dev, streamed: bool = False):
+    opt = _PcgOptions(float(tol), int(max_iter), int(rhs_sign), 0, 1 if streamed else 0)
     _check(load().agipc_pcg_mixed(ctx.handle, int(max_rows), _ptr(n_rows_dev), _ptr(row_ptr), _ptr(col), _ptr(val),
                                   _ptr(val32), _ptr(dinv32), _ptr(b), _ptr(x), ctypes.byref(opt), int(refine_every),
                                   _ptr(iters_dev), _ptr(relres_dev)), "agipc_pcg_mixed")
@@ -331,12 +331,13 @@ class CoarsenedStep:
     """Output buffers of one coarsened Newton-step solve and the four calls
     that fill them: aggregate -> assemble_coarse -> pcg -> prolongate."""
 
-    def __init__(self, ctx: Context, ds: DeviceScene, tol: float, max_iter: int = 100000):
+    def __init__(self, ctx: Context, ds: DeviceScene, tol: float, max_iter: int = 100000, streamed: bool = False):
         dev = ds.g.device
         n, cap = ds.n, ds.capacity
         i32 = dict(device=dev, dtype=torch.int32)
         f64 = dict(device=dev, dtype=torch.float64)
         self.ctx, self.ds, self.tol, self.max_iter = ctx, ds, tol, max_iter
+        self.streamed = streamed   # the 16-warp streaming PCG (systems larger than shared memory)
         self.labels = torch.empty(n, **i32)
         self.n_c = torch.zeros(1, **i32)
         self.row_ptr = torch.empty(n + 1, **i32)
@@ -361,7 +362,7 @@ class CoarsenedStep:
 
     def solve(self):
         agipc_pcg(self.ctx, self.ds.n, self.n_c, self.row_ptr, self.col, self.val, self.dinv, self.g_c, self.y,
-                  self.tol, self.max_iter, -1, self.iters, self.relres)
+                  self.tol, self.max_iter, -1, self.iters, self.relres, streamed=self.streamed)
 
     def prolongate(self):
         agipc_prolongate(self.ctx, self.ds.n, self.labels, self.y, self.dx)
@@ -472,8 +473,8 @@ class MixedStep(CoarsenedStep):
     iterations against the FP64 master coarse matrix."""
 
     def __init__(self, ctx: Context, ds: MixedDeviceScene, tol: float, max_iter: int = 100000,
-                 refine_every: int = 20):
-        super().__init__(ctx, ds, tol, max_iter)
+                 refine_every: int = 20, streamed: bool = False):
+        super().__init__(ctx, ds, tol, max_iter, streamed=streamed)
         self.refine_every = refine_every
         self.val32 = torch.empty(ds.capacity, 9, device=ds.g.device, dtype=torch.float32)
         self.dinv32 = torch.empty(ds.n, 9, device=ds.g.device, dtype=torch.float32)
@@ -486,7 +487,8 @@ class MixedStep(CoarsenedStep):
 
     def solve(self):
         agipc_pcg_mixed(self.ctx, self.ds.n, self.n_c, self.row_ptr, self.col, self.val, self.val32, self.dinv32,
-                        self.g_c, self.y, self.tol, self.max_iter, -1, self.refine_every, self.iters, self.relres)
+                        self.g_c, self.y, self.tol, self.max_iter, -1, self.refine_every, self.iters, self.relres,
+                        streamed=self.streamed)
 
     def host(self):
         out = super().host()
@@ -502,8 +504,8 @@ class MixedFineStep:
     residual replacement against the FP64 master."""
 
     def __init__(self, ctx: Context, ds: MixedDeviceScene, tol: float, max_iter: int = 100000,
-                 refine_every: int = 20):
-        self.inner = MixedStep(ctx, ds, tol, max_iter, refine_every)
+                 refine_every: int = 20, streamed: bool = True):
+        self.inner = MixedStep(ctx, ds, tol, max_iter, refine_every, streamed=streamed)
         self.inner.labels.copy_(torch.arange(ds.n, dtype=torch.int32, device=ds.g.device))
         self.inner.n_c.fill_(ds.n)
 
@@ -536,7 +538,7 @@ class PostCoarsening:
         f = self.fine.inner
         self.x.copy_(dx)
         agipc_pcg(self.ctx, self.ds.n, f.n_c, f.row_ptr, f.col, f.val, f.dinv, f.g_c, self.x, self.tol, self.max_iter,
-                  -1, f.iters, f.relres, use_x0=True)
+                  -1, f.iters, f.relres, use_x0=True, streamed=f.streamed)
         return self.x
 
 
@@ -544,8 +546,8 @@ class FineStep:
     """The no-coarsening arm: identity labels (the fine system in full
     storage, contacts merged) and PCG on the fine matrix."""
 
-    def __init__(self, ctx: Context, ds: DeviceScene, tol: float, max_iter: int = 100000):
-        self.inner = CoarsenedStep(ctx, ds, tol, max_iter)
+    def __init__(self, ctx: Context, ds: DeviceScene, tol: float, max_iter: int = 100000, streamed: bool = True):
+        self.inner = CoarsenedStep(ctx, ds, tol, max_iter, streamed=streamed)
         self.inner.labels.copy_(torch.arange(ds.n, dtype=torch.int32, device=ds.g.device))
         self.inner.n_c.fill_(ds.n)
 

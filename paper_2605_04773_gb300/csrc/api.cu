@@ -10,6 +10,8 @@ int pcg_block_size();
 int pcg_smem_bytes();
 const void *pcg_kernel_ptr();
 const void *pcg_mixed_kernel_ptr();
+bool pcg_mixed_wide_configure();
+bool pcg_wide_configure();
 int assemble_long_row_ctas();
 bool batched_configure(agipc_ctx *c);
 
@@ -131,7 +133,8 @@ extern "C" int agipc_create(agipc_ctx **out, void *cuda_stream, int32_t max_fine
     c->pcg_block = pcg_block_size();
     c->pcg_grid = std::min(std::min(per_sm, per_sm_mixed), cap_per_sm) * c->num_sms;
     c->pcg.max_grid = c->pcg_grid;
-    if (!batched_configure(c)) {
+    if (c->num_sms > c->pcg.max_grid || !pcg_wide_configure() || !pcg_mixed_wide_configure() ||
+        !batched_configure(c)) {
         delete c;
         return AGIPC_ERR_CUDA;
     }

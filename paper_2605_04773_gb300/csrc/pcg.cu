@@ -105,18 +105,36 @@ __device__ __forceinline__ void row_update(int64_t i, const double uu[3], const 
     }
 }
 
-__global__ void __launch_bounds__(kPcgBlock, 1) pcg_kernel(PcgArgs A)
+// Shared-memory layout of the two variants.  kW = 8 warps (up to 255
+// registers): each warp owns two slice buffers; a matrix whose slices fit one
+// per warp is held there for the whole solve (resident mode), a larger one
+// streams through both buffers.  kW = 16 warps (at most 128 registers): twice
+// the warps keep the FP64 pipe fed while others wait for their slices; each
+// warp's region holds one slice and the matrix always streams.
+template <int kW>
+struct PcgGeom {
+    static constexpr bool kWide = kW > kPcgWarps;
+    static constexpr int kBufArea = kWide ? kBufBytes : 2 * kBufBytes;   // slice buffers of one warp
+    static constexpr int kRegion = kBufArea + kJoinBytes;
+    static constexpr int kSmem = kW * kRegion + 32 * kW * 3 * 8;          // + the CTA-sum slots
+    static_assert(kRegion % 16 == 0, "16-byte aligned slice buffers");
+};
+
+template <int kW>
+__global__ void __launch_bounds__(32 * kW, 1) pcg_kernel(PcgArgs A)
 {
+    using Geo = PcgGeom<kW>;
+    constexpr bool kWide = Geo::kWide;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_scal[2];
     __shared__ double s_tot[4];
     __shared__ double s_grid[4];
-    __shared__ double s_gr[2 * kPcgBlock];   // the P phase's per-thread gamma, rho shares
+    __shared__ double s_gr[2 * 32 * kW];   // the P phase's per-thread gamma, rho shares
     __shared__ int s_dec;
 
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const unsigned nblocks = gridDim.x;
-    const int64_t nwarps = (int64_t)nblocks * kPcgWarps;
+    const int64_t nwarps = (int64_t)nblocks * kW;
     const int64_t gwarp = (int64_t)wib * nblocks + blockIdx.x;  // slices interleave over CTAs
     const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
 
@@ -131,12 +149,14 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_kernel(PcgArgs A)
         return;
     }
     const int64_t nslices = div_up(nnz, kSlice);
-    const bool resident = nslices <= nwarps;  // every warp keeps at most one slice in shared memory
+    // every warp keeps at most one slice in shared memory
+    const bool resident = !kWide && nslices <= nwarps;
     // rows owned by this CTA in the row-local phases
     const int64_t rows_per_cta = div_up(n, nblocks);
     const int64_t row0 = min64((int64_t)blockIdx.x * rows_per_cta, n);
     const int64_t row1 = min64(row0 + rows_per_cta, n);
-    const bool one_row = rows_per_cta <= kPcgBlock;  // row state can be fetched ahead of the barrier
+    // row state can be fetched ahead of the barrier (the 8-warp variant)
+    const bool one_row = !kWide && rows_per_cta <= kPcgBlock;
 
     double *__restrict__ r = A.S.r;
     double *u = A.S.u;
@@ -153,9 +173,9 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_kernel(PcgArgs A)
     const int mg = A.S.max_grid;
     const int pstride = mg * 4;
     unsigned epoch = 0;
-    unsigned char *wbuf = smem + (size_t)wib * kWarpSmem;
-    unsigned char *join = wbuf + 2 * kBufBytes;
-    double *s_part = reinterpret_cast<double *>(smem + (size_t)kPcgWarps * kWarpSmem);
+    unsigned char *wbuf = smem + (size_t)wib * Geo::kRegion;
+    unsigned char *join = wbuf + Geo::kBufArea;
+    double *s_part = reinterpret_cast<double *>(smem + (size_t)kW * Geo::kRegion);
 
     // ---- setup: block rows, split flags, x = 0 (or the given x0), r = b - A x0,
     // u = M^-1 r, p = s = w = 0; with x0 the residual needs A x0, so it is
@@ -233,7 +253,7 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_kernel(PcgArgs A)
     }
     {
         double v[3] = {gpart, rpart, bpart};
-        cta_sum<3>(v, s_part, s_tot);
+        cta_sum<3, kW>(v, s_part, s_tot);
         if (threadIdx.x == 0) {
             partials[0 * mg + blockIdx.x] = v[0];
             partials[1 * mg + blockIdx.x] = v[1];
@@ -262,41 +282,66 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_kernel(PcgArgs A)
         double *part = partials + par * pstride;
         // ---- S phase: w = A u, partial delta
         double dpart = 0.0;
-        for (int64_t sl = gwarp; sl < nslices; sl += nwarps) {
-            if (!resident) {
-                // stream the next slice of this iteration, or the first slice of
-                // the next one, into the other buffer while this one is used
-                const int64_t next = sl + nwarps < nslices ? sl + nwarps : gwarp;
-                issue_slice(wbuf + (nb ^ 1) * kBufBytes, next, nnz, A.val, A.col, brow, lane);
-                cp_async_commit();
-                cp_async_wait<1>();
-            } else {
+        if constexpr (kWide) {
+            // one buffer: the warp's first slice was issued at the end of the
+            // previous iteration (it loads during the grid barrier), each later
+            // one after the warp has multiplied with the one before; the other
+            // warps keep the FP64 pipe busy meanwhile
+            for (int64_t sl = gwarp; sl < nslices; sl += nwarps) {
+                if (sl != gwarp) {
+                    issue_slice(wbuf, sl, nnz, A.val, A.col, brow, lane);
+                    cp_async_commit();
+                }
                 cp_async_wait<0>();
+                __syncwarp();
+                const int cnt = (int)min64(kSlice, nnz - sl * kSlice);
+                slice_spmv<double, true>(wbuf, cnt, u, w, rowflag, join, lane, dpart);
             }
-            __syncwarp();
-            const int cnt = (int)min64(kSlice, nnz - sl * kSlice);
-            slice_spmv<double, true>(wbuf + nb * kBufBytes, cnt, u, w, rowflag, join, lane, dpart);
-            if (!resident) nb ^= 1;
+        } else {
+            for (int64_t sl = gwarp; sl < nslices; sl += nwarps) {
+                if (!resident) {
+                    // stream the next slice of this iteration, or the first slice
+                    // of the next one, into the other buffer while this one is used
+                    const int64_t next = sl + nwarps < nslices ? sl + nwarps : gwarp;
+                    issue_slice(wbuf + (nb ^ 1) * kBufBytes, next, nnz, A.val, A.col, brow, lane);
+                    cp_async_commit();
+                    cp_async_wait<1>();
+                } else {
+                    cp_async_wait<0>();
+                }
+                __syncwarp();
+                const int cnt = (int)min64(kSlice, nnz - sl * kSlice);
+                slice_spmv<double, true>(wbuf + nb * kBufBytes, cnt, u, w, rowflag, join, lane, dpart);
+                if (!resident) nb ^= 1;
+            }
         }
-        if (it > 0 && wib == kPcgWarps - 1) {
+        if (it > 0 && wib == kW - 1) {
             // the previous P phase's gamma and rho shares, summed over the CTA
             // (fixed order) by the last warp, which holds the fewest slices, so
             // the sum overlaps the other warps' SpMV instead of delaying the
             // barrier after the P phase
-            double t0[kPcgWarps], t1[kPcgWarps];
+            // (eight warps' slots at a time: a tree of three levels each, the
+            // groups added in order; with one group a0 = 0 + tree is the tree)
+            double a0 = 0.0, a1 = 0.0;
 #pragma unroll
-            for (int q = 0; q < kPcgWarps; ++q) {
-                t0[q] = s_gr[2 * (lane + 32 * q)];
-                t1[q] = s_gr[2 * (lane + 32 * q) + 1];
-            }
+            for (int g = 0; g < kW; g += 8) {
+                double t0[8], t1[8];
 #pragma unroll
-            for (int h = kPcgWarps / 2; h > 0; h >>= 1)
-#pragma unroll
-                for (int q = 0; q < h; ++q) {
-                    t0[q] += t0[q + h];
-                    t1[q] += t1[q + h];
+                for (int q = 0; q < 8; ++q) {
+                    t0[q] = s_gr[2 * (lane + 32 * (g + q))];
+                    t1[q] = s_gr[2 * (lane + 32 * (g + q)) + 1];
                 }
-            const double g0 = warp_sum(t0[0]), g1 = warp_sum(t1[0]);
+#pragma unroll
+                for (int h = 4; h > 0; h >>= 1)
+#pragma unroll
+                    for (int q = 0; q < h; ++q) {
+                        t0[q] += t0[q + h];
+                        t1[q] += t1[q + h];
+                    }
+                a0 += t0[0];
+                a1 += t1[0];
+            }
+            const double g0 = warp_sum(a0), g1 = warp_sum(a1);
             if (lane == 0) {
                 part[0 * mg + blockIdx.x] = g0;
                 part[1 * mg + blockIdx.x] = g1;
@@ -321,7 +366,7 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_kernel(PcgArgs A)
         }
         {
             double v[1] = {dpart};
-            cta_sum<1>(v, s_part, s_tot);
+            cta_sum<1, kW>(v, s_part, s_tot);
             if (threadIdx.x == 0) part[2 * mg + blockIdx.x] = v[0];
         }
         if (!grid_sync(count, nblocks, epoch, A.status)) { ok = false; break; }
@@ -421,7 +466,7 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_kernel(PcgArgs A)
         } else {
             // kRows rows per thread per pass: every load of the pass is
             // issued before the first store, so their latencies overlap
-            constexpr int kRows = 2;
+            constexpr int kRows = kWide ? 1 : 2;
             for (int64_t i0 = row0 + threadIdx.x; i0 < row1; i0 += kRows * (int64_t)blockDim.x) {
                 double uu[kRows][3], ww[kRows][3], pp[kRows][3], ss[kRows][3], rr[kRows][3], xx[kRows][3];
                 double D[kRows][9];
@@ -455,6 +500,11 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_kernel(PcgArgs A)
         s_gr[2 * threadIdx.x] = gpart;
         s_gr[2 * threadIdx.x + 1] = rpart;
         ++it;
+        if constexpr (kWide) {
+            // the next S phase's first slice loads during the barrier
+            if (gwarp < nslices) issue_slice(wbuf, gwarp, nnz, A.val, A.col, brow, lane);
+            cp_async_commit();
+        }
         if (!grid_sync(count, nblocks, epoch, A.status)) { ok = false; break; }
     }
     cp_async_wait<0>();
@@ -477,7 +527,20 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_kernel(PcgArgs A)
 int pcg_block_size() { return kPcgBlock; }
 int pcg_smem_bytes() { return kPcgSmem; }
 
-const void *pcg_kernel_ptr() { return reinterpret_cast<const void *>(&pcg_kernel); }
+const void *pcg_kernel_ptr() { return reinterpret_cast<const void *>(&pcg_kernel<kPcgWarps>); }
+
+// The 16-warp streaming variant runs one CTA per SM; false if the SM cannot
+// hold it (its shared memory or registers).
+bool pcg_wide_configure()
+{
+    constexpr int kW = 2 * kPcgWarps;
+    const void *k = reinterpret_cast<const void *>(&pcg_kernel<kW>);
+    int per_sm = 0;
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, PcgGeom<kW>::kSmem) ==
+               cudaSuccess &&
+           cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 32 * kW, PcgGeom<kW>::kSmem) == cudaSuccess &&
+           per_sm >= 1;
+}
 
 extern "C" int agipc_pcg(agipc_ctx *ctx, int32_t max_rows, const int32_t *n_rows_dev, const int32_t *row_ptr,
                          const int32_t *col, const double *val, const double *dinv, const double *b, double *x,
@@ -511,7 +574,15 @@ extern "C" int agipc_pcg(agipc_ctx *ctx, int32_t max_rows, const int32_t *n_rows
     A.status = ctx->status;
     if (cudaMemsetAsync(ctx->pcg.bar, 0, 64 * sizeof(unsigned), ctx->stream) != cudaSuccess) return AGIPC_ERR_CUDA;
     void *args[] = {&A};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void *)pcg_kernel, dim3((unsigned)ctx->pcg_grid),
-                                                dim3(kPcgBlock), args, kPcgSmem, ctx->stream);
+    static_assert(PcgGeom<kPcgWarps>::kSmem == kPcgSmem, "the 8-warp layout is the shared PCG layout");
+    cudaError_t e;
+    if (opt->streamed) {
+        constexpr int kW = 2 * kPcgWarps;
+        e = cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(&pcg_kernel<kW>), dim3((unsigned)ctx->num_sms),
+                                        dim3(32 * kW), args, PcgGeom<kW>::kSmem, ctx->stream);
+    } else {
+        e = cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(&pcg_kernel<kPcgWarps>),
+                                        dim3((unsigned)ctx->pcg_grid), dim3(kPcgBlock), args, kPcgSmem, ctx->stream);
+    }
     return e == cudaSuccess ? AGIPC_OK : AGIPC_ERR_CUDA;
 }

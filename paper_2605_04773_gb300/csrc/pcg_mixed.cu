@@ -50,21 +50,49 @@ __device__ __forceinline__ void precond32(const float *D, const double r[3], flo
     for (int c = 0; c < 3; ++c) u[c] = fmaf(D[3 * c + 2], r2, fmaf(D[3 * c + 1], r1, D[3 * c] * r0));
 }
 
-__global__ void __launch_bounds__(kPcgBlock, 1) pcg_mixed_kernel(MixedArgs A)
+// Shared-memory layout of the two variants.  kW = 8 warps (255 registers):
+// each warp owns a region of two FP64 slice buffers; a matrix that fits is
+// held there for the whole solve (resident mode), a larger one streams
+// through a ring of three FP32 slices.  kW = 16 warps (at most 128
+// registers): twice the warps to hide the latency of a streamed matrix; each
+// warp's region holds a ring of two FP32 slices (or one FP64 slice of a
+// residual replacement) and the matrix always streams.
+template <int kW>
+struct MixedGeom {
+    static constexpr bool kWide = kW > kPcgWarps;
+    static constexpr int kRing = kWide ? 2 : 3;
+    static constexpr int kB32 = SliceLayout<float>::kBuf;
+    static constexpr int kB64 = SliceLayout<double>::kBuf;
+    static constexpr int kBufArea = kWide ? kRing * kB32 : 2 * kBufBytes;   // slice buffers of one warp
+    static constexpr int kRegion = kBufArea + kJoinBytes;
+    static constexpr int kSmem = kW * kRegion + 32 * kW * 3 * 8;            // + the CTA-sum slots
+    static_assert(kRing * kB32 <= kBufArea && (kWide ? kB64 : 2 * kB64) <= kBufArea &&
+                      (kWide || kB32 + kB64 <= kBufArea) && kB32 % 16 == 0 && kB64 % 16 == 0 &&
+                      kRegion % 16 == 0,
+                  "slice buffers overflow the warp's region");
+};
+
+template <int kW>
+__global__ void __launch_bounds__(32 * kW, 1) pcg_mixed_kernel(MixedArgs A)
 {
+    using Geo = MixedGeom<kW>;
+    constexpr bool kWide = Geo::kWide;
+    constexpr int kRing = Geo::kRing;
+    constexpr int kB32 = Geo::kB32;
+    constexpr int kB64 = Geo::kB64;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_scal[2];
     __shared__ double s_tot[4];
     __shared__ double s_grid[3];
-    __shared__ double s_gr[2 * kPcgBlock];   // the P phase's per-thread gamma, rho shares
+    __shared__ double s_gr[2 * 32 * kW];   // the P phase's per-thread gamma, rho shares
     __shared__ int s_dec;
     __shared__ bool s_ref;
     __shared__ int s_abort;
-    __shared__ __align__(8) uint64_t s_mbar[kPcgWarps * 3];   // one per ring slot of each warp
+    __shared__ __align__(8) uint64_t s_mbar[kW * kRing];   // one per ring slot of each warp
 
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const unsigned nblocks = gridDim.x;
-    const int64_t nwarps = (int64_t)nblocks * kPcgWarps;
+    const int64_t nwarps = (int64_t)nblocks * kW;
     const int64_t gwarp = (int64_t)wib * nblocks + blockIdx.x;  // slices interleave over CTAs
     const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
 
@@ -79,7 +107,7 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_mixed_kernel(MixedArgs A)
         return;
     }
     const int64_t nslices = div_up(nnz, kSlice);
-    const bool resident = nslices <= nwarps;
+    const bool resident = !kWide && nslices <= nwarps;
     const int64_t rows_per_cta = div_up(n, nblocks);
     const int64_t row0 = min64((int64_t)blockIdx.x * rows_per_cta, n);
     const int64_t row1 = min64(row0 + rows_per_cta, n);
@@ -104,9 +132,9 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_mixed_kernel(MixedArgs A)
     const int mg = A.S.max_grid;
     const int pstride = mg * 4;
     unsigned epoch = 0;
-    unsigned char *wbuf = smem + (size_t)wib * kWarpSmem;
-    unsigned char *join = wbuf + 2 * kBufBytes;
-    double *s_part = reinterpret_cast<double *>(smem + (size_t)kPcgWarps * kWarpSmem);
+    unsigned char *wbuf = smem + (size_t)wib * Geo::kRegion;
+    unsigned char *join = wbuf + Geo::kBufArea;
+    double *s_part = reinterpret_cast<double *>(smem + (size_t)kW * Geo::kRegion);
 
     // ---- setup
     double gpart = 0.0, rpart = 0.0;
@@ -143,7 +171,7 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_mixed_kernel(MixedArgs A)
     }
     {
         double v[2] = {gpart, rpart};
-        cta_sum<2>(v, s_part, s_tot);
+        cta_sum<2, kW>(v, s_part, s_tot);
         if (threadIdx.x == 0) {
             partials[0 * mg + blockIdx.x] = v[0];
             partials[1 * mg + blockIdx.x] = v[1];
@@ -161,19 +189,12 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_mixed_kernel(MixedArgs A)
     // while it multiplies with another; the first kRing - 1 slices of an S
     // phase are issued at the end of the previous iteration, so they load
     // during the grid barrier.  The FP64 slices of a residual replacement
-    // double-buffer over the ring's region.
-    constexpr int kRing = 3;
-    constexpr int kB32 = SliceLayout<float>::kBuf;
-    constexpr int kB64 = SliceLayout<double>::kBuf;
-    static_assert(kRing * kB32 <= 2 * kBufBytes && kB32 + kB64 <= 2 * kBufBytes && 2 * kB64 <= 2 * kBufBytes &&
-                      kB32 % 16 == 0 && kB64 % 16 == 0,
-                  "slice buffers overflow the warp's region");
+    // go over the ring's region (double-buffered where two fit).
     // A full slice goes by TMA bulk copy and completes on its slot's
     // mbarrier; the ragged last slice of the matrix goes by the zero-filling
     // cp.async path (a bulk copy would need lengths rounded up to 16 bytes,
     // past the caller's arrays).  `ph` holds each slot's next parity, `pend`
     // the slots with a bulk copy in flight (drained before the kernel ends).
-    static_assert(kRing == 3, "one mbarrier per ring slot");
     uint64_t *mbar = s_mbar + kRing * wib;
     unsigned ph = 0, pend = 0;
     if (threadIdx.x == 0) s_abort = 0;
@@ -240,12 +261,12 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_mixed_kernel(MixedArgs A)
                 slice_compute<float, true>(wbuf, G, w, join, lane, dpart);
             }
         } else {
+          if constexpr (kRing == 3) {
             // The k-th slice of the warp sits in ring slot k mod kRing.  While
             // slice k is multiplied, the gathers of slice k + 1 (landed) are in
             // flight and slice k + 2 loads into the slot slice k - 1 used.
             // Two gather sets alternate (no copies between them, which would
             // wait for the loads in flight).
-            static_assert(kRing == 3, "the gather pipeline holds three slices");
             SliceGather<float> G0, G1;
             int slot = 0;
             if (gwarp < nslices) {
@@ -270,18 +291,33 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_mixed_kernel(MixedArgs A)
                 step(sl, G0, G1);
                 if (sl + nwarps < nslices) step(sl + nwarps, G1, G0);
             }
+          } else {
+            // Two slots: slice k + 1 loads into the slot slice k - 1 used while
+            // slice k is gathered and multiplied (the other warps hide the
+            // gathers' latency).
+            int slot = 0;
+            for (int64_t sl = gwarp; sl < nslices; sl += nwarps) {
+                const int64_t nx = sl + nwarps;
+                if (nx < nslices) ring_issue(slot ^ 1, nx);
+                ring_wait(slot, sl);
+                SliceGather<float> G;
+                slice_gather_packed(wbuf + slot * kB32, (int)min64(kSlice, nnz - sl * kSlice), u4, lane, G);
+                slice_compute<float, true>(wbuf + slot * kB32, G, w, join, lane, dpart);
+                slot ^= 1;
+            }
+          }
         }
-        if (pending && wib == kPcgWarps - 1) {
+        if (pending && wib == kW - 1) {
             // the previous P phase's gamma and rho shares, summed over the CTA
             // (fixed order) by the last warp while the others multiply
-            double t0[kPcgWarps], t1[kPcgWarps];
+            double t0[kW], t1[kW];
 #pragma unroll
-            for (int q = 0; q < kPcgWarps; ++q) {
+            for (int q = 0; q < kW; ++q) {
                 t0[q] = s_gr[2 * (lane + 32 * q)];
                 t1[q] = s_gr[2 * (lane + 32 * q) + 1];
             }
 #pragma unroll
-            for (int h = kPcgWarps / 2; h > 0; h >>= 1)
+            for (int h = kW / 2; h > 0; h >>= 1)
 #pragma unroll
                 for (int q = 0; q < h; ++q) {
                     t0[q] += t0[q + h];
@@ -295,7 +331,7 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_mixed_kernel(MixedArgs A)
         }
         {
             double v[1] = {dpart};
-            cta_sum<1>(v, s_part, s_tot);
+            cta_sum<1, kW>(v, s_part, s_tot);
             if (threadIdx.x == 0) part[2 * mg + blockIdx.x] = v[0];
         }
         if (s_abort) { ok = false; break; }   // a slice never arrived (ST_TIMEOUT is set)
@@ -409,7 +445,7 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_mixed_kernel(MixedArgs A)
         } else {
             // kRows rows per thread per pass: every load of the pass is issued
             // before the first store, so their latencies overlap
-            constexpr int kRows = 2;
+            constexpr int kRows = kWide ? 1 : 2;
             for (int64_t i0 = row0 + threadIdx.x; i0 < row1; i0 += kRows * (int64_t)blockDim.x) {
                 float uu[kRows][3], ww[kRows][3], pp[kRows][3], ss[kRows][3], D[kRows][9];
                 double xx[kRows][3], rr[kRows][3];
@@ -488,6 +524,16 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_mixed_kernel(MixedArgs A)
                     const int cnt = (int)min64(kSlice, nnz - gwarp * kSlice);
                     slice_spmv<double, false>(fb, cnt, x, ax, rowflag, join, lane, dummy);
                 }
+            } else if constexpr (kWide) {
+                // one FP64 slice at a time over the (empty) ring's region
+                for (int64_t sl = gwarp; sl < nslices; sl += nwarps) {
+                    issue_slice(wbuf, sl, nnz, A.val64, A.col, brow, lane);
+                    cp_async_commit();
+                    cp_async_wait<0>();
+                    __syncwarp();
+                    const int cnt = (int)min64(kSlice, nnz - sl * kSlice);
+                    slice_spmv<double, false>(wbuf, cnt, x, ax, rowflag, join, lane, dummy);
+                }
             } else {
                 // the ring is empty here (the next S phase's slices are issued
                 // after this pass)
@@ -543,7 +589,20 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_mixed_kernel(MixedArgs A)
 
 }  // namespace
 
-const void *pcg_mixed_kernel_ptr() { return reinterpret_cast<const void *>(&pcg_mixed_kernel); }
+const void *pcg_mixed_kernel_ptr() { return reinterpret_cast<const void *>(&pcg_mixed_kernel<kPcgWarps>); }
+
+// The 16-warp streaming variant runs one CTA per SM; false if the SM cannot
+// hold it (its shared memory or registers).
+bool pcg_mixed_wide_configure()
+{
+    constexpr int kW = 2 * kPcgWarps;
+    const void *k = reinterpret_cast<const void *>(&pcg_mixed_kernel<kW>);
+    int per_sm = 0;
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, MixedGeom<kW>::kSmem) ==
+               cudaSuccess &&
+           cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 32 * kW, MixedGeom<kW>::kSmem) == cudaSuccess &&
+           per_sm >= 1;
+}
 
 extern "C" int agipc_pcg_mixed(agipc_ctx *ctx, int32_t max_rows, const int32_t *n_rows_dev, const int32_t *row_ptr,
                                const int32_t *col, const double *val, const float *val32, const float *dinv32,
@@ -579,7 +638,16 @@ extern "C" int agipc_pcg_mixed(agipc_ctx *ctx, int32_t max_rows, const int32_t *
     A.status = ctx->status;
     if (cudaMemsetAsync(ctx->pcg.bar, 0, 64 * sizeof(unsigned), ctx->stream) != cudaSuccess) return AGIPC_ERR_CUDA;
     void *args[] = {&A};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void *)pcg_mixed_kernel, dim3((unsigned)ctx->pcg_grid),
-                                                dim3(kPcgBlock), args, kPcgSmem, ctx->stream);
+    static_assert(MixedGeom<kPcgWarps>::kSmem == kPcgSmem, "the 8-warp layout is the shared PCG layout");
+    cudaError_t e;
+    if (opt->streamed) {
+        constexpr int kW = 2 * kPcgWarps;
+        e = cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(&pcg_mixed_kernel<kW>),
+                                        dim3((unsigned)ctx->num_sms), dim3(32 * kW), args, MixedGeom<kW>::kSmem,
+                                        ctx->stream);
+    } else {
+        e = cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(&pcg_mixed_kernel<kPcgWarps>),
+                                        dim3((unsigned)ctx->pcg_grid), dim3(kPcgBlock), args, kPcgSmem, ctx->stream);
+    }
     return e == cudaSuccess ? AGIPC_OK : AGIPC_ERR_CUDA;
 }

@@ -115,25 +115,24 @@ __device__ __forceinline__ void issue_slice(unsigned char *buf, int64_t sl, int6
     }
 }
 
-// Sum of N values per thread over the CTA: threads park their values in
-// shared memory, warp 0 adds them with a tree (3 levels over the 8 warps,
-// then 5 shuffle levels).  The result is valid in thread 0.
-template <int N>
+// Sum of N values per thread over a CTA of kW warps: threads park their
+// values in shared memory, warp k adds value k (each warp sits on its own SM
+// sub-partition, whose FP64 pipe is the bottleneck) with a tree over the kW
+// warps' slots, then 5 shuffle levels.  Totals land in v for every thread.
+template <int N, int kW = kPcgWarps>
 __device__ __forceinline__ void cta_sum(double (&v)[N], double *s_part, double *s_out)
 {
-    // Warp k adds value k (each warp sits on its own SM sub-partition, whose
-    // FP64 pipe is the bottleneck): 3 tree levels over the 8 warps' slots,
-    // then 5 shuffle levels.  Totals land in s_out[0..N) for every thread.
+    static_assert(N <= kW, "one warp per value");
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < N; ++k) s_part[N * threadIdx.x + k] = v[k];
     __syncthreads();
     if (wid < N) {
-        double t[kPcgWarps];
+        double t[kW];
 #pragma unroll
-        for (int q = 0; q < kPcgWarps; ++q) t[q] = s_part[N * (lane + 32 * q) + wid];
+        for (int q = 0; q < kW; ++q) t[q] = s_part[N * (lane + 32 * q) + wid];
 #pragma unroll
-        for (int h = kPcgWarps / 2; h > 0; h >>= 1)
+        for (int h = kW / 2; h > 0; h >>= 1)
 #pragma unroll
             for (int q = 0; q < h; ++q) t[q] += t[q + h];
         const double tot = warp_sum(t[0]);

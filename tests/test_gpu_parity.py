@@ -210,12 +210,14 @@ def test_domino_full_size_parity(domino_full):
     _check_solve(got, crp, cci, cval, gc, 1e-6)
 
 
-def test_fine_arm_full_size(domino_full):
-    """Identity labels: the fine system in full storage and fine PCG to 1e-6."""
+@pytest.mark.parametrize("streamed", [False, True])
+def test_fine_arm_full_size(domino_full, streamed):
+    """Identity labels: the fine system in full storage and fine PCG to 1e-6,
+    in both kernel layouts (2.28 M blocks: both stream it from HBM)."""
     sc = domino_full
     ds = agipc.DeviceScene(sc)
     ctx = ds.context()
-    fs = agipc.FineStep(ctx, ds, tol=1e-6)
+    fs = agipc.FineStep(ctx, ds, tol=1e-6, streamed=streamed)
     fs.run()
     assert ctx.status() == agipc.OK
     got = fs.host()
@@ -309,8 +311,9 @@ def test_pcg_deterministic():
     ctx.close()
 
 
+@pytest.mark.parametrize("streamed", [False, True])
 @pytest.mark.parametrize("seed", [1001, 1011])
-def test_post_coarsening_matches_oracle_cg_from_dx(seed):
+def test_post_coarsening_matches_oracle_cg_from_dx(seed, streamed):
     # Sec. 4.3: at most 10 fine PCG iterations started from the prolongated
     # coarse step.  Both sides start from the oracle's dx (an input here),
     # run exactly 10 iterations, and must agree; CG never raises the energy.
@@ -323,6 +326,7 @@ def test_post_coarsening_matches_oracle_cg_from_dx(seed):
     ds = agipc.DeviceScene(sc)
     ctx = ds.context()
     post = agipc.PostCoarsening(ctx, ds, tol=1e-14, max_iter=10)
+    post.fine.inner.streamed = streamed
     post.assemble()
     x = post.refine(torch.tensor(ref["dx"], dtype=torch.float64, device=ds.g.device))
     rc = ctx.status()
@@ -340,6 +344,35 @@ def test_post_coarsening_matches_oracle_cg_from_dx(seed):
         return g @ v.reshape(-1) + 0.5 * v.reshape(-1) @ oracle.spmv(rp, ci, val, v).reshape(-1)
 
     assert energy(got) <= energy(ref["dx"]) + 1e-12 * abs(energy(ref["dx"]))
+
+
+@pytest.mark.parametrize("streamed", [False, True])
+@pytest.mark.parametrize("case", ["unit_cube", "domino_4x4"])
+def test_fine_pcg_both_layouts(case, streamed):
+    # FP64 PCG on a fine system (identity labels) in both kernel layouts: 8
+    # warps per SM (the unit cube stays in shared memory; the 4x4 domino's
+    # 330,332 blocks = 2,581 slices exceed the 1,216 it holds and stream) and
+    # 16 warps per SM (always streamed, one slice buffer per warp: the unit
+    # cube leaves most warps idle, the domino gives some warps two slices and
+    # ends in a ragged 92-block slice).  Structure bit-exact, true residual.
+    if case == "unit_cube":
+        sc = scenes.unit_cube(seed=1001)
+    else:
+        sc = scenes.domino_grid(seed=1003, gx=4, gy=4, dims=(8, 8, 16), n_pairs=20000, small_gap_frac=0.02)
+    tol = 1e-8
+    ds = agipc.DeviceScene(sc)
+    ctx = ds.context()
+    fs = agipc.FineStep(ctx, ds, tol=tol, streamed=streamed)
+    fs.run()
+    assert ctx.status() == agipc.OK
+    got = fs.host()
+    ctx.close()
+    frp, fci, fval = oracle.fine_system(sc)
+    assert np.array_equal(got["row_ptr"], frp) and np.array_equal(got["col"], fci)
+    if case == "domino_4x4":
+        assert frp[-1] > 1216 * 128 and frp[-1] % 128 != 0
+    res = oracle.spmv(frp, fci, fval, got["y"]) + sc.g
+    assert np.linalg.norm(res) <= 1.05 * tol * np.linalg.norm(sc.g)
 
 
 def test_pcg_initial_guess_zero_rhs_returns_zero():

@@ -155,3 +155,48 @@ def test_precision_form_c3_errors_vs_fp64_oracle():
     print("C3 vs FP64 oracle: coarse residual %.3e (bound %.3e), dx rel err %.3e, energy decrease rel err %.3e"
           % (res, bound, dx_err, e_err))
     assert dx_err < 1e-3 and e_err < 1e-6
+
+
+def _fine_mixed(sc, tol, streamed):
+    ds = agipc.MixedDeviceScene(sc)
+    ctx = ds.context()
+    st = agipc.MixedFineStep(ctx, ds, tol=tol, streamed=streamed)
+    st.assemble()
+    ctx.check()
+    st.solve()
+    rc = ctx.status()
+    out = st.host()
+    ctx.close()
+    assert rc == agipc.OK, (rc, out["iters"], out["relres"])
+    return out
+
+
+@pytest.mark.parametrize("streamed", [False, True])
+@pytest.mark.parametrize("case", ["unit_cube", "domino_4x4"])
+def test_precision_form_fine_system_both_layouts(case, streamed):
+    # The precision-form PCG on a fine system (identity labels, contacts
+    # merged) in both kernel layouts: 8 warps per SM (the unit cube's matrix
+    # stays in shared memory; the 4x4 domino's 330,332 blocks = 2,581 slices
+    # exceed the 1,216 it holds and stream) and 16 warps per SM (always
+    # streamed: the unit cube leaves most warps without a slice, the domino
+    # gives some warps two, and its last slice is ragged, 92 blocks, so it
+    # takes the zero-filling copy path while full slices go by bulk copy).
+    # Judged by the true FP64 residual with the oracle's fine matrix of the
+    # same rounded inputs.
+    if case == "unit_cube":
+        sc = scenes.unit_cube(seed=1001)
+    else:
+        sc = scenes.domino_grid(seed=1003, gx=4, gy=4, dims=(8, 8, 16), n_pairs=20000, small_gap_frac=0.02)
+    tol = 1e-8
+    got = _fine_mixed(sc, tol, streamed)
+    pi = precision.scene_split(sc)
+    ident = np.arange(sc.n, dtype=np.int32)
+    pidx = np.concatenate([pi["pair_idx32"], pi["pair_idx64"]])
+    pblk = np.concatenate([pi["pair_blk32"].astype(np.float64), pi["pair_blk64"]])
+    crp, cci, cval = oracle.galerkin(ident, sc.n, sc.row_ptr, sc.col, pi["val32"].astype(np.float64), pidx, pblk)
+    assert np.array_equal(got["row_ptr"], crp) and np.array_equal(got["col"], cci)
+    if case == "domino_4x4":
+        assert crp[-1] > 1216 * 128 and crp[-1] % 128 != 0
+    g = sc.g.reshape(-1, 3)
+    rel = np.linalg.norm(oracle.spmv(crp, cci, cval, got["y"]) + g) / np.linalg.norm(g)
+    assert rel <= 1.05 * tol, rel
