@@ -166,6 +166,14 @@ def pcg_bytes_per_iter(nnzb: int, n: int) -> int:
     return 76 * nnzb + 200 * n
 
 
+def pcg_mixed_bytes_per_iter(nnzb: int, n: int, refine_every: int = 20) -> float:
+    """The same for the precision form: 40 B per block (9 FP32 values and a
+    column index) and 240 B per row (FP32 u, w, p, s, FP64 x, r, FP32
+    preconditioner), plus the FP64 residual replacement every refine_every
+    iterations (76 B per block and 96 B per row)."""
+    return 40 * nnzb + 240 * n + (76 * nnzb + 96 * n) / refine_every
+
+
 def fp64_probe():
     """Build and run fp64_unit_probe.cu (nvcc, sm_103a): the measured FP64
     FMA rate of one SM, returned as parsed JSON."""
@@ -334,8 +342,11 @@ def run_ours(args):
                        "relres": res["relres"], "pcg_ms": 1e3 * pcg_avg_s,
                        "step_ms_median": float(np.median(step_ms))},
             "fine_pcg": {"value": 1e3 / float(np.median(fine_ms)), "unit": UNIT, "ms_per_step": float(np.median(fine_ms)),
+                         "kernel": "pcg_kernel, 16 warps per SM, matrix streamed from HBM (fine assembly included "
+                                   "in ms_per_step)",
                          "pcg_iters": fine_iters, "nnzb": fine_nnz, "relres": fres["relres"],
                          "hbm_gbs_pcg_algorithmic": fine_pcg_bytes / (float(np.median(fine_ms)) / 1e3) / 1e9,
+                         "hbm_frac_pcg_algorithmic": fine_pcg_bytes / (float(np.median(fine_ms)) / 1e3) / 1e9 / peak,
                          "fp64_tflops_pcg_algorithmic": fine_iters * pcg_flops_per_iter(fine_nnz, sc.n) /
                                                          (float(np.median(fine_ms)) / 1e3) / 1e12,
                          "speedup_of_coarsened": float(np.median(fine_ms)) / (1e3 * total_s / args.steps)},
@@ -491,7 +502,14 @@ def precision_form(ctx_factory, dev, steps: int):
                             "mixed_iters": mf_it, "fp64_iters": f64_it, "mixed_relres": mf_res,
                             "speedup": float(np.median(f64_ms)) / float(np.median(f32_ms)),
                             "mixed_us_per_iter": 1e3 * float(np.median(f32_ms)) / max(mf_it, 1),
-                            "fp64_us_per_iter": 1e3 * float(np.median(f64_ms)) / max(f64_it, 1)}}
+                            "fp64_us_per_iter": 1e3 * float(np.median(f64_ms)) / max(f64_it, 1),
+                            "kernels": "16 warps per SM, matrix streamed from HBM",
+                            "mixed_hbm_frac": pcg_mixed_bytes_per_iter(fnnz, sc.n) * mf_it /
+                                              (float(np.median(f32_ms)) / 1e3) / 1e9 / _peaks()[0],
+                            "fp64_hbm_frac": pcg_bytes_per_iter(fnnz, sc.n) * f64_it /
+                                             (float(np.median(f64_ms)) / 1e3) / 1e9 / _peaks()[0],
+                            "byte_models": "FP64: 76 B per block + 200 B per row; precision form: 40 B per block "
+                                           "+ 240 B per row + (76 B per block + 96 B per row) / 20"}}
 
 
 def differentiation_form(dev, steps: int):

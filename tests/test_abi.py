@@ -62,3 +62,20 @@ def test_binding_fails_loudly_without_gpu():
         pytest.skip("a GPU is present")
     with pytest.raises(RuntimeError):
         agipc.Context(10, 10, 10, 0)
+
+
+def test_pcg_options_layout_matches_header():
+    # agipc_pcg_options in include/agipc.h: double tol; int32 max_iter,
+    # rhs_sign, use_x0, streamed -- 24 bytes, 'streamed' in what was the
+    # struct's tail padding.  The binding's ctypes copy must match it field
+    # by field, and the header must declare the fields in that order.
+    from paper_2605_04773_gb300 import agipc
+    O = agipc._PcgOptions
+    assert ctypes.sizeof(O) == 24
+    assert [(n, getattr(O, n).offset) for n, _ in O._fields_] == [
+        ("tol", 0), ("max_iter", 8), ("rhs_sign", 12), ("use_x0", 16), ("streamed", 20)]
+    hdr = open(os.path.join(ROOT, "include", "agipc.h")).read()
+    body = hdr[hdr.index("typedef struct {", hdr.index("PCG options")):hdr.index("} agipc_pcg_options;")]
+    fields = re.findall(r"^\s*(double|int32_t)\s+(\w+);", body, re.M)
+    assert fields == [("double", "tol"), ("int32_t", "max_iter"), ("int32_t", "rhs_sign"), ("int32_t", "use_x0"),
+                      ("int32_t", "streamed")]
