@@ -57,33 +57,45 @@ __device__ __forceinline__ double spmv(const unsigned char *buf, int qlo, int cn
     const T *s_val = reinterpret_cast<const T *>(buf);
     const int32_t *s_col = reinterpret_cast<const int32_t *>(buf + G::kValBytes);
     const int32_t *s_row = reinterpret_cast<const int32_t *>(buf + G::kValBytes + G::kIdxBytes);
+    // The gathers are plain (L1-cacheable) loads: u and the flags are written
+    // only in other phases, each followed by a grid barrier whose acquire
+    // orders those writes before these loads.  The flag byte is kept as
+    // loaded and tested where it is used.
     int rows_[K];
     T xv[K][3];
     T ur[K][3];
-    bool split[K];
+    int flags[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) {
         const int q = lane * K + j;
         rows_[j] = -1;
-        split[j] = false;
+        flags[j] = 0;
         xv[j][0] = xv[j][1] = xv[j][2] = T(0);
         ur[j][0] = ur[j][1] = ur[j][2] = T(0);
         if (q >= qlo && q < cnt) {
             const int rj = s_row[q];
             rows_[j] = rj;
             const T *uc = u + 3 * (int64_t)s_col[q];
-            xv[j][0] = __ldcg(uc);
-            xv[j][1] = __ldcg(uc + 1);
-            xv[j][2] = __ldcg(uc + 2);
+            xv[j][0] = uc[0];
+            xv[j][1] = uc[1];
+            xv[j][2] = uc[2];
             if (j == 0 || q == qlo || rj != s_row[q - 1]) {  // first block of a row segment
                 const T *up = u + 3 * (int64_t)rj;
-                ur[j][0] = __ldcg(up);
-                ur[j][1] = __ldcg(up + 1);
-                ur[j][2] = __ldcg(up + 2);
-                split[j] = (__ldcg(rowflag + rj) & 1) != 0;
+                ur[j][0] = up[0];
+                ur[j][1] = up[1];
+                ur[j][2] = up[2];
+                flags[j] = rowflag[rj];
             }
         }
     }
+    // Values: when the lane's K blocks start on a 16-byte boundary (9 K
+    // sizeof(T) a multiple of 16: K = 4, 8 in FP32, even K in FP64) they are
+    // read chunk by chunk with pcgs::load_chunk (144-byte chunks of 4 FP32 or
+    // 2 FP64 blocks, 16-byte loads, no bank conflicts at that stride); other
+    // widths read scalars.
+    constexpr int kBpc = 16 / (int)sizeof(T);
+    constexpr bool kChunked = (9 * K * (int)sizeof(T)) % 16 == 0 && K % kBpc == 0;
+    T ch[9 * kBpc];
     T acc[3] = {T(0), T(0), T(0)};
     T fa[3] = {T(0), T(0), T(0)}, la[3] = {T(0), T(0), T(0)};
     T fu[3] = {T(0), T(0), T(0)}, lu[3] = {T(0), T(0), T(0)};
@@ -98,17 +110,23 @@ __device__ __forceinline__ double spmv(const unsigned char *buf, int qlo, int cn
         const bool end = valid && (j == K - 1 || rows_[j + 1] != rows_[j]);
         // positions outside [qlo, cnt) read stale or foreign shared memory:
         // select zeros for them
-        const T *Bs = s_val + 9 * (lane * K + j);
         T B[9];
+        if constexpr (kChunked) {
+            if (j % kBpc == 0) pcgs::load_chunk(s_val + 9 * (lane * K + j), ch);
 #pragma unroll
-        for (int e = 0; e < 9; ++e) B[e] = dsel(valid, Bs[e], T(0));
+            for (int e = 0; e < 9; ++e) B[e] = dsel(valid, ch[9 * (j % kBpc) + e], T(0));
+        } else {
+            const T *Bs = s_val + 9 * (lane * K + j);
+#pragma unroll
+            for (int e = 0; e < 9; ++e) B[e] = dsel(valid, Bs[e], T(0));
+        }
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             cu[c] = dsel(start, ur[j][c], cu[c]);
             acc[c] = dsel(start, T(0), acc[c]);
             acc[c] = fma(B[3 * c + 2], xv[j][2], fma(B[3 * c + 1], xv[j][1], fma(B[3 * c], xv[j][0], acc[c])));
         }
-        s_cur = start ? split[j] : s_cur;
+        s_cur = start ? (flags[j] & 1) != 0 : s_cur;
         if (end) {
             const bool last = j == K - 1 || rows_[j + 1] < 0;
             if (first_open) {
