@@ -688,6 +688,7 @@ def batched_form(dev, steps: int, peak_gbs: float, n_inst: int = 256, ws: int = 
     med_step = float(np.median(step_ms))
     out = {"value": 1e3 / med_step, "unit": "batches/s", "instances_per_s": batch.n_inst * 1e3 / med_step,
            "ms_per_batch": med_step, "pcg_ms": med_pcg, "tile_blocks_per_lane": tile, "autotune_ms": tune_ms,
+           "assembly_terms_per_lane": st.assembly_run, "autotune_assembly_ms": st.assembly_ms,
            "n_inst": batch.n_inst, "n_fine": batch.n, "n_tets": int(batch.tets.shape[0]),
            "fine_upper_nnzb": int(batch.col.shape[0]), "n_pairs": int(batch.pair_idx.shape[0]),
            "n_c": h["n_c"], "nnzb_c": int(rp[-1]), "iters_min_median_max": [int(it.min()), int(np.median(it)),

@@ -77,6 +77,18 @@ int agipc_destroy(agipc_ctx *ctx);
 int agipc_set_stream(agipc_ctx *ctx, void *cuda_stream);
 
 /*
+ * Launch shape of the coarse assembly's reduction (the numeric phase of
+ * agipc_assemble_coarse and agipc_assemble_coarse_mixed, supplement Sec. 2):
+ * each lane folds terms_per_lane consecutive sorted terms into running 3x3
+ * blocks before flushing them with atomics (a warp covers 32 x that many).
+ * Longer runs mean fewer atomics inside large super-nodes but a longer
+ * serial chain per lane.  4, 8 (the default) or 16; anything else returns
+ * AGIPC_ERR_INVALID_ARG.  The results agree to rounding order (the atomics'
+ * order changes).  Applies to later calls on the context.
+ */
+int agipc_set_assembly_run(agipc_ctx *ctx, int32_t terms_per_lane);
+
+/*
  * Super-node labels (Sec. 4.1: nodes are coalesced only across paths of
  * collapsible edges; supplement Sec. 1, Algorithms 1-2 and the worked
  * examples of Sec. 1.2-1.3).

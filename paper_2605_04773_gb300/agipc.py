@@ -62,6 +62,7 @@ def load():
     lib.agipc_create.argtypes = [ctypes.POINTER(P), P, i32, i64, i64, i64]
     lib.agipc_destroy.argtypes = [P]
     lib.agipc_set_stream.argtypes = [P, P]
+    lib.agipc_set_assembly_run.argtypes = [P, ctypes.c_int32]
     lib.agipc_aggregate.argtypes = [P, i32, i64, P, P, P, P]
     lib.agipc_assemble_coarse.argtypes = [P, i32, P, P, P, P, P, i64, i64, P, P, P, P, P, P, i64, P, P, P]
     lib.agipc_pcg.argtypes = [P, i32, P, P, P, P, P, P, P, ctypes.POINTER(_PcgOptions), P, P]
@@ -91,8 +92,8 @@ def load():
     lib.agipc_max_abs.argtypes = [P, i64, P, P]
     lib.agipc_status_string.argtypes = [ctypes.c_int]
     lib.agipc_status_string.restype = ctypes.c_char_p
-    for name in ("agipc_create", "agipc_destroy", "agipc_set_stream", "agipc_aggregate", "agipc_assemble_coarse",
-                 "agipc_pcg", "agipc_prolongate", "agipc_status", "agipc_aggregate_static",
+    for name in ("agipc_create", "agipc_destroy", "agipc_set_stream", "agipc_set_assembly_run", "agipc_aggregate",
+                 "agipc_assemble_coarse", "agipc_pcg", "agipc_prolongate", "agipc_status", "agipc_aggregate_static",
                  "agipc_assemble_coarse_mixed", "agipc_pcg_mixed", "agipc_precision_split", "agipc_prolongate_add", "agipc_fine_assemble_stvk",
                  "agipc_restrict", "agipc_stvk_vjp", "agipc_batch_coarse_offsets", "agipc_pcg_batched", "agipc_strain_tags", "agipc_affine_plan", "agipc_assemble_affine",
                  "agipc_prolongate_affine", "agipc_stvk_energy", "agipc_max_abs"):
@@ -140,6 +141,12 @@ class Context:
     def set_stream(self, stream):
         self.stream = stream
         _check(load().agipc_set_stream(self.handle, ctypes.c_void_p(stream.cuda_stream)), "agipc_set_stream")
+
+    def set_assembly_run(self, terms_per_lane: int):
+        """agipc_set_assembly_run: terms per lane of the coarse assembly's
+        reduction (4, 8 or 16)."""
+        _check(load().agipc_set_assembly_run(self.handle, int(terms_per_lane)), "agipc_set_assembly_run")
+        self.assembly_run = int(terms_per_lane)
 
     def status(self) -> int:
         """Synchronize and return (and clear) the device-side status."""
@@ -269,6 +276,7 @@ def agipc_max_abs(ctx: Context, v, out_dev):
 
 BATCH_MAX_INSTANCES = 512
 BATCH_TILES = (4, 5, 6, 8)
+ASSEMBLY_RUNS = (4, 8, 16)   # terms per lane of the coarse assembly's reduction
 
 
 def agipc_batch_coarse_offsets(ctx: Context, n_inst: int, n_fine: int, vert_ptr, labels, n_coarse_dev, inst_row):
@@ -915,11 +923,15 @@ class BatchedStep:
         bd, ctx = self.bd, self.ctx
         agipc_aggregate(ctx, bd.n, bd.edges, bd.tags, self.labels, self.n_c)
         agipc_batch_coarse_offsets(ctx, bd.n_inst, bd.n, bd.vert_ptr, self.labels, self.n_c, self.inst_row)
-        agipc_assemble_coarse_mixed(ctx, bd.n, self.labels, self.n_c, bd.row_ptr, bd.col, bd.val32, bd.pair_idx,
-                                    bd.pair_blk32, bd.pair_idx64, bd.pair_blk64, bd.g, self.row_ptr, self.col,
-                                    self.val, self.val32, self.nnz, self.g_c, self.dinv32)
+        self.assemble()
         self.solve()
         agipc_prolongate(ctx, bd.n, self.labels, self.y, self.dx)
+
+    def assemble(self):
+        bd = self.bd
+        agipc_assemble_coarse_mixed(self.ctx, bd.n, self.labels, self.n_c, bd.row_ptr, bd.col, bd.val32, bd.pair_idx,
+                                    bd.pair_blk32, bd.pair_idx64, bd.pair_blk64, bd.g, self.row_ptr, self.col,
+                                    self.val, self.val32, self.nnz, self.g_c, self.dinv32)
 
     def solve(self, tile: int = None):
         agipc_pcg_batched(self.ctx, self.bd.n_inst, self.inst_row, self.bd.n, self.row_ptr, self.col, self.val,
@@ -957,11 +969,15 @@ class BatchedStep:
                     relres=self.relres.cpu().numpy())
 
 
-def autotune_batched(step: BatchedStep, tiles=BATCH_TILES, reps: int = 3, cache: str = None):
-    """Pick the batched PCG's slice width by timing each candidate on the
-    step's own coarse systems (after one run()), median of reps launches.
-    The choice is cached per device and batch shape in a JSON file (default:
-    next to the library) and set on the step.  Returns (tile, timings_ms)."""
+def autotune_batched(step: BatchedStep, tiles=BATCH_TILES, runs=ASSEMBLY_RUNS, reps: int = 3, cache: str = None):
+    """Pick the batched form's two launch shapes by timing each candidate on
+    the step's own systems after one run(), median of reps launches: the
+    coarse assembly's reduction run (terms per lane, agipc_set_assembly_run;
+    the assembly alone on the step's labels) and the batched PCG's slice
+    width (the solve alone).  The choices are cached per device and batch
+    shape in a JSON file (default: next to the library) and set on the step
+    and its context.  Returns (tile, timings_ms); the run and its timings
+    are in step.assembly_run and step.assembly_ms."""
     import json
     dev = step.bd.g.device
     key = "%s|n_inst=%d|n=%d|nnzb=%d" % (torch.cuda.get_device_name(dev), step.bd.n_inst, step.bd.n,
@@ -973,27 +989,42 @@ def autotune_batched(step: BatchedStep, tiles=BATCH_TILES, reps: int = 3, cache:
             table = json.load(open(path))
         except (OSError, ValueError):
             table = {}
-    if key in table and table[key]["tile"] in tiles:
-        step.tile = int(table[key]["tile"])
-        return step.tile, table[key]["ms"]
+    ent = table.get(key)
+    if ent and ent.get("tile") in tiles and ent.get("assembly_run") in runs:
+        step.tile = int(ent["tile"])
+        step.ctx.set_assembly_run(int(ent["assembly_run"]))
+        step.assembly_run, step.assembly_ms = int(ent["assembly_run"]), ent["assembly_ms"]
+        return step.tile, ent["ms"]
     step.run()
     step.ctx.check()
     stream = torch.cuda.current_stream(dev)
-    ms = {}
-    for tile in tiles:
+
+    def median_ms(fn):
         times = []
         for _ in range(reps):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            step.solve(tile)
+            fn()
             b.record(stream)
             torch.cuda.synchronize(dev)
             times.append(a.elapsed_time(b))
         step.ctx.check()
-        ms[str(tile)] = float(np.median(times))
+        return float(np.median(times))
+
+    asm_ms = {}
+    for r in runs:
+        step.ctx.set_assembly_run(r)
+        asm_ms[str(r)] = median_ms(step.assemble)
+    run = int(min(asm_ms, key=asm_ms.get))
+    step.ctx.set_assembly_run(run)
+    step.assemble()
+    ms = {}
+    for tile in tiles:
+        ms[str(tile)] = median_ms(lambda: step.solve(tile))
     best = int(min(ms, key=ms.get))
     step.tile = best
-    table[key] = {"tile": best, "ms": ms}
+    step.assembly_run, step.assembly_ms = run, asm_ms
+    table[key] = {"tile": best, "ms": ms, "assembly_run": run, "assembly_ms": asm_ms}
     try:
         with open(path + ".tmp", "w") as f:
             json.dump(table, f, indent=1)

@@ -73,6 +73,9 @@ struct agipc_ctx {
     int pcg_block;
     int pcg_grid;
 
+    // coarse assembly: terms each lane of the numeric phase folds (4, 8, 16)
+    int asm_run;
+
     // batched PCG
     double *batch_acc;                // [6 * kBatchMaxInst] per-instance sums
     int batch_grid[kBatchVariants];   // cooperative grid of each slice-width variant

@@ -53,6 +53,8 @@ def test_null_context_is_rejected_on_host(lib):
     assert lib.agipc_prolongate(None, 10, None, None, None) == -1
     lib.agipc_create.argtypes = [P, P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
     assert lib.agipc_create(None, None, 1, 1, 1, 1) == -1
+    lib.agipc_set_assembly_run.argtypes = [P, ctypes.c_int32]
+    assert lib.agipc_set_assembly_run(None, 8) == -1
 
 
 def test_binding_fails_loudly_without_gpu():

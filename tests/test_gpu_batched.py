@@ -120,7 +120,7 @@ def test_graph_replay_matches_eager():
         _check_instance(batch, rep, i)
 
 
-def test_autotuner_picks_a_tile(tmp_path):
+def test_autotuner_picks_both_launch_shapes(tmp_path):
     agipc = _agipc()
     batch = scenes.batch_instances(seed=2006, n_inst=16, v_range=(500, 4000), with_values=True)
     bd = agipc.BatchDevice(batch)
@@ -128,8 +128,15 @@ def test_autotuner_picks_a_tile(tmp_path):
     st = agipc.BatchedStep(ctx, bd, tol=TOL)
     tile, ms = agipc.autotune_batched(st, cache=str(tmp_path / "tune.json"))
     assert tile in agipc.BATCH_TILES and set(ms) == {str(t) for t in agipc.BATCH_TILES}
+    run = st.assembly_run
+    assert run in agipc.ASSEMBLY_RUNS and set(st.assembly_ms) == {str(r) for r in agipc.ASSEMBLY_RUNS}
+    assert ctx.assembly_run == run
+    # the cache holds both launch shapes and a second call reuses them
+    import json
+    ent = next(iter(json.load(open(tmp_path / "tune.json")).values()))
+    assert ent["tile"] == tile and ent["assembly_run"] == run
     tile2, _ = agipc.autotune_batched(st, cache=str(tmp_path / "tune.json"))
-    assert tile2 == tile
+    assert tile2 == tile and st.assembly_run == run
     st.run()
     assert ctx.status() == 0
     got = st.host()
