@@ -82,7 +82,8 @@ int agipc_set_stream(agipc_ctx *ctx, void *cuda_stream);
  * each lane folds terms_per_lane consecutive sorted terms into running 3x3
  * blocks before flushing them with atomics (a warp covers 32 x that many).
  * Longer runs mean fewer atomics inside large super-nodes but a longer
- * serial chain per lane.  4, 8 (the default) or 16; anything else returns
+ * serial chain per lane.  4, 8, 16 or 32 (the default: the fastest on the
+ * 64-box domino's coarse assembly on GB300); anything else returns
  * AGIPC_ERR_INVALID_ARG.  The results agree to rounding order (the atomics'
  * order changes).  Applies to later calls on the context.
  */

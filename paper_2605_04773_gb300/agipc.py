@@ -144,7 +144,7 @@ class Context:
 
     def set_assembly_run(self, terms_per_lane: int):
         """agipc_set_assembly_run: terms per lane of the coarse assembly's
-        reduction (4, 8 or 16)."""
+        reduction (4, 8, 16 or 32)."""
         _check(load().agipc_set_assembly_run(self.handle, int(terms_per_lane)), "agipc_set_assembly_run")
         self.assembly_run = int(terms_per_lane)
 
@@ -276,7 +276,7 @@ def agipc_max_abs(ctx: Context, v, out_dev):
 
 BATCH_MAX_INSTANCES = 512
 BATCH_TILES = (4, 5, 6, 8)
-ASSEMBLY_RUNS = (4, 8, 16)   # terms per lane of the coarse assembly's reduction
+ASSEMBLY_RUNS = (4, 8, 16, 32)   # terms per lane of the coarse assembly's reduction
 
 
 def agipc_batch_coarse_offsets(ctx: Context, n_inst: int, n_fine: int, vert_ptr, labels, n_coarse_dev, inst_row):

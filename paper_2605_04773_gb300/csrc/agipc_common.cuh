@@ -73,7 +73,7 @@ struct agipc_ctx {
     int pcg_block;
     int pcg_grid;
 
-    // coarse assembly: terms each lane of the numeric phase folds (4, 8, 16)
+    // coarse assembly: terms each lane of the numeric phase folds (4, 8, 16, 32)
     int asm_run;
 
     // batched PCG

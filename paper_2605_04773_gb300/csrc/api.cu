@@ -131,7 +131,7 @@ extern "C" int agipc_create(agipc_ctx **out, void *cuda_stream, int32_t max_fine
     int cap_per_sm = 2;
     if (const char *env = std::getenv("AGIPC_PCG_CTAS_PER_SM")) cap_per_sm = std::max(1, std::atoi(env));
     c->pcg_block = pcg_block_size();
-    c->asm_run = 8;
+    c->asm_run = 32;
     c->pcg_grid = std::min(std::min(per_sm, per_sm_mixed), cap_per_sm) * c->num_sms;
     c->pcg.max_grid = c->pcg_grid;
     if (c->num_sms > c->pcg.max_grid || !pcg_wide_configure() || !pcg_mixed_wide_configure() ||
@@ -176,7 +176,7 @@ extern "C" int agipc_set_stream(agipc_ctx *ctx, void *cuda_stream)
 
 extern "C" int agipc_set_assembly_run(agipc_ctx *ctx, int32_t terms_per_lane)
 {
-    if (!ctx || (terms_per_lane != 4 && terms_per_lane != 8 && terms_per_lane != 16)) return AGIPC_ERR_INVALID_ARG;
+    if (!ctx || (terms_per_lane != 4 && terms_per_lane != 8 && terms_per_lane != 16 && terms_per_lane != 32)) return AGIPC_ERR_INVALID_ARG;
     ctx->asm_run = terms_per_lane;
     return AGIPC_OK;
 }

@@ -411,7 +411,7 @@ __device__ __forceinline__ void flush_run(unsigned long long key, const double a
 // with atomics when it changes.  If all 32 lanes end on the same key the warp
 // reduces it with shuffles first, so a large super-node's diagonal block
 // receives one atomic set per 32 x kRun terms instead of one per term.
-// kRun (4, 8 or 16) is the context's launch shape (agipc_set_assembly_run).
+// kRun (4, 8, 16 or 32) is the context's launch shape (agipc_set_assembly_run).
 template <int kRun>
 __global__ void __launch_bounds__(kTb) numeric_kernel(TermArgs A, const int32_t *__restrict__ row_ptr,
                                                       const int32_t *__restrict__ col, int64_t cap, double *val,
@@ -623,16 +623,19 @@ static int assemble_impl(agipc_ctx *ctx, int32_t n_fine, const int32_t *fine_row
                                                        coarse_row_ptr, coarse_col, coarse_cap_nnzb, ctx->bitmap,
                                                        ctx->bitmap_words);
     zero_outputs_kernel<<<grid_sm, kTb, 0, st>>>(n_coarse_dev, coarse_nnzb_dev, coarse_cap_nnzb, coarse_val, g_c);
-    const int run = ctx->asm_run == 4 || ctx->asm_run == 16 ? ctx->asm_run : 8;
+    const int run = ctx->asm_run == 4 || ctx->asm_run == 8 || ctx->asm_run == 16 ? ctx->asm_run : 32;
     const unsigned gnum = (unsigned)std::min<int64_t>(div_up(n_terms > 0 ? n_terms : 1, (int64_t)kTb * run),
                                                       (int64_t)grid_sm * 4);
     if (run == 4)
         numeric_kernel<4><<<gnum, kTb, 0, st>>>(A, coarse_row_ptr, coarse_col, coarse_cap_nnzb, coarse_val, ctx->status);
+    else if (run == 8)
+        numeric_kernel<8><<<gnum, kTb, 0, st>>>(A, coarse_row_ptr, coarse_col, coarse_cap_nnzb, coarse_val, ctx->status);
     else if (run == 16)
         numeric_kernel<16><<<gnum, kTb, 0, st>>>(A, coarse_row_ptr, coarse_col, coarse_cap_nnzb, coarse_val,
                                                  ctx->status);
     else
-        numeric_kernel<8><<<gnum, kTb, 0, st>>>(A, coarse_row_ptr, coarse_col, coarse_cap_nnzb, coarse_val, ctx->status);
+        numeric_kernel<32><<<gnum, kTb, 0, st>>>(A, coarse_row_ptr, coarse_col, coarse_cap_nnzb, coarse_val,
+                                                 ctx->status);
     mirror_kernel<<<gw, kTb, 0, st>>>(n_coarse_dev, coarse_row_ptr, coarse_col, coarse_cap_nnzb, coarse_val,
                                       ctx->status);
     dinv_kernel<<<(unsigned)std::min<int64_t>(div_up(n_fine, kTb), (int64_t)grid_sm * 4), kTb, 0, st>>>(

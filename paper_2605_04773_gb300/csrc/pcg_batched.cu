@@ -554,13 +554,18 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_batched_kernel(BatchArgs A)
             const int64_t rw[2] = {iA, iB};
             const int in_[2] = {instA, instB};
             const bool ok2[2] = {okA, okB};
-            float uu[2][3], ww[2][3], pp[2][3], ss[2][3];
+            float uu[2][3], ww[2][3], pp[2][3], ss[2][3], D[2][9];
             double xx[2][3], rr[2][3];
-            // loads of both rows first
+            bool fl[2] = {false, false};
+            // every load of both rows first (the flag byte and the
+            // preconditioner too: after a store the compiler may not move
+            // them up, a byte or float load could alias it)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                if (!ok2[h] || s_dec[in_[h]] != 0) continue;
+                if (!ok2[h]) continue;
                 const int64_t i = rw[h];
+                fl[h] = rowflag[i] != 0;
+                if (s_dec[in_[h]] != 0) continue;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     uu[h][c] = __ldcg(u + 3 * i + c);
@@ -570,6 +575,10 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_batched_kernel(BatchArgs A)
                     xx[h][c] = x[3 * i + c];
                     rr[h][c] = r[3 * i + c];
                 }
+                if (!s_ref[in_[h]]) {
+#pragma unroll
+                    for (int e = 0; e < 9; ++e) D[h][e] = A.dinv32[9 * i + e];
+                }
             }
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -577,7 +586,7 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_batched_kernel(BatchArgs A)
                 const int64_t i = rw[h];
                 const int inst = in_[h];
                 const int dec = s_dec[inst];
-                const bool flagged = rowflag[i] != 0;
+                const bool flagged = fl[h];
                 if (dec == 4) {
                     // verify: no Krylov step; only clear what receives atomics
                     if (flagged) {
@@ -613,7 +622,7 @@ __global__ void __launch_bounds__(kPcgBlock, 1) pcg_batched_kernel(BatchArgs A)
                 }
                 if (!ref) {
                     float un[3];
-                    precond32(A.dinv32 + 9 * i, rn, un);
+                    precond32(D[h], rn, un);
                     double gi = 0.0, ri = 0.0;
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {

@@ -193,7 +193,7 @@ def test_single_supernode_and_all_protected():
     _check_solve(got, crp, cci, cval, gc, 1e-8)
 
 
-@pytest.mark.parametrize("assembly_run", [4, 8, 16])
+@pytest.mark.parametrize("assembly_run", [4, 8, 16, 32])
 def test_domino_small_multibody(assembly_run):
     # every launch shape of the coarse reduction (terms per lane) meets the
     # same per-entry bar: only the order of the atomics changes
