@@ -149,7 +149,8 @@ typedef struct {
     int32_t rhs_sign;    /* +1 or -1 */
     int32_t use_x0;      /* agipc_pcg only: nonzero = x holds the initial guess on entry (else x0 = 0);
                             the stop test stays relative to ||b||; b = 0 gives x = 0 */
-    int32_t streamed;    /* kernel layout (results are the same up to rounding order).  0: 8 warps per SM,
+    int32_t streamed;    /* agipc_pcg and agipc_pcg_mixed (agipc_pcg_batched ignores it): kernel layout
+                            (results are the same up to rounding order).  0: 8 warps per SM,
                             the matrix held in shared memory when its 128-block slices fit one per warp
                             (1216 slices on 152 SMs), streamed from HBM every iteration otherwise.
                             Nonzero: 16 warps per SM and the matrix always streamed; for systems larger
