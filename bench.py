@@ -275,7 +275,7 @@ def run_ours(args):
     dx_host = torch.empty_like(step.dx, device="cpu").pin_memory()
     d2h = dx_host.numel() * dx_host.element_size()
     pipe = agipc.HostPipeline(ctx, (ds, agipc.DeviceScene(sc, dev)), tol=TOL)
-    e2e_steps = max(3, min(10, args.steps))
+    e2e_steps = max(3, min(20, args.steps))
     pipe.run([host_in] * 2, [dx_host] * 2)   # warm-up of the second buffer set
     torch.cuda.synchronize(dev)
     ctx.check()

@@ -398,10 +398,10 @@ SCENE_INPUTS = ("edges", "tags", "row_ptr", "col", "val", "pair_idx", "pair_blk"
 class HostPipeline:
     """Coarsened steps whose inputs arrive in pinned host memory, one after
     another, as a serving loop runs them: two sets of device input buffers;
-    the host-to-device copies of step k+1 run on a copy stream while step k's
-    kernels run on the context's stream, and each step's dx is copied back
-    to the host.  Both steps share the context (their kernels are ordered on
-    its stream)."""
+    the host-to-device copies of step k+1 and the device-to-host copy of
+    step k-1's dx run on a copy stream while step k's kernels run on the
+    context's stream.  Both steps share the context (their kernels are
+    ordered on its stream)."""
 
     def __init__(self, ctx: Context, buffers, tol: float, max_iter: int = 100000):
         if len(buffers) != 2:
@@ -410,8 +410,9 @@ class HostPipeline:
         self.bufs = tuple(buffers)
         self.steps = [CoarsenedStep(ctx, b, tol, max_iter) for b in self.bufs]
         self.copy_stream = torch.cuda.Stream(device=self.bufs[0].g.device)
-        self.copied = [torch.cuda.Event() for _ in range(2)]
-        self.free = [torch.cuda.Event() for _ in range(2)]
+        self.copied = [torch.cuda.Event() for _ in range(2)]   # inputs of buffer set i are on the device
+        self.free = [torch.cuda.Event() for _ in range(2)]     # buffer set i's step has run
+        self.read = [torch.cuda.Event() for _ in range(2)]     # its dx has reached the host
 
     def run(self, host_inputs, dx_out):
         """Enqueue len(host_inputs) steps.  host_inputs[k] maps every name of
@@ -423,10 +424,11 @@ class HostPipeline:
         n = len(host_inputs)
         if len(dx_out) != n:
             raise ValueError("one dx buffer per step")
-        for e in self.free:
+        for e in self.free + self.read:
             e.record(comp)
 
         def issue(k):
+            # step k's inputs, once buffer set k % 2's previous step has run
             i = k % 2
             self.copy_stream.wait_event(self.free[i])
             with torch.cuda.stream(self.copy_stream):
@@ -441,10 +443,14 @@ class HostPipeline:
             if k + 1 < n:
                 issue(k + 1)
             comp.wait_event(self.copied[i])
+            comp.wait_event(self.read[i])     # step k-2's dx has left steps[i].dx
             self.steps[i].run()
-            with torch.cuda.stream(comp):
-                dx_out[k].copy_(self.steps[i].dx, non_blocking=True)
             self.free[i].record(comp)
+            self.copy_stream.wait_event(self.free[i])
+            with torch.cuda.stream(self.copy_stream):
+                dx_out[k].copy_(self.steps[i].dx, non_blocking=True)
+            self.read[i].record(self.copy_stream)
+        comp.wait_stream(self.copy_stream)    # the caller's synchronisation covers the last copies
 
 
 class MixedDeviceScene(DeviceScene):
