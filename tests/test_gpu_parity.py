@@ -37,12 +37,12 @@ def domino_full():
     return scenes.domino_grid(seed=1002)
 
 
-def _run(sc, tags=None, tol=1e-8, max_iter=100000, assembly_run=None):
+def _run(sc, tags=None, tol=1e-8, max_iter=100000, assembly_run=None, streamed=False):
     ds = agipc.DeviceScene(sc)
     ctx = ds.context()
     if assembly_run is not None:
         ctx.set_assembly_run(assembly_run)
-    step = agipc.CoarsenedStep(ctx, ds, tol=tol, max_iter=max_iter)
+    step = agipc.CoarsenedStep(ctx, ds, tol=tol, max_iter=max_iter, streamed=streamed)
     if tags is not None:
         step.aggregate(torch.from_numpy(np.ascontiguousarray(tags, np.uint8)).cuda())
         step.assemble()
@@ -151,9 +151,12 @@ def test_labels_no_edges():
 # ------------------------------------------------------------------ full path
 
 
-def test_unit_cube_full_path_parity():
+@pytest.mark.parametrize("streamed", [False, True])
+def test_unit_cube_full_path_parity(streamed):
+    # streamed: the 16-warp kernel on a 60-block coarse system, one ragged
+    # slice for the whole GPU (every other warp idle)
     sc = scenes.unit_cube(seed=1001)
-    rc, got = _run(sc, tol=1e-8)
+    rc, got = _run(sc, tol=1e-8, streamed=streamed)
     assert rc == agipc.OK
     crp, cci, cval, gc = _check_coarse(sc, got, sc.tags)
     _check_solve(got, crp, cci, cval, gc, 1e-8)
@@ -266,11 +269,12 @@ def test_host_pipeline_matches_single_steps():
     ctx.close()
 
 
-def test_status_not_converged_and_zero_rhs():
+@pytest.mark.parametrize("streamed", [False, True])
+def test_status_not_converged_and_zero_rhs(streamed):
     sc = scenes.unit_cube(seed=1001)
     ds = agipc.DeviceScene(sc)
     ctx = ds.context()
-    step = agipc.CoarsenedStep(ctx, ds, tol=1e-12, max_iter=1)
+    step = agipc.CoarsenedStep(ctx, ds, tol=1e-12, max_iter=1, streamed=streamed)
     step.run()
     assert ctx.status() == agipc.ERR_NOT_CONVERGED
     assert int(step.iters.item()) == 1

@@ -29,10 +29,10 @@ def _lib():
     agipc.load()
 
 
-def _mixed(sc, tol):
+def _mixed(sc, tol, streamed=False):
     ds = agipc.MixedDeviceScene(sc)
     ctx = ds.context()
-    st = agipc.MixedStep(ctx, ds, tol=tol)
+    st = agipc.MixedStep(ctx, ds, tol=tol, streamed=streamed)
     stages = {}
     for name, f in (("aggregate", st.aggregate), ("assemble", st.assemble), ("solve", st.solve),
                     ("prolongate", st.prolongate)):
@@ -65,9 +65,12 @@ def _check(sc, got, tol):
     return rel
 
 
-def test_precision_form_unit_cube():
+@pytest.mark.parametrize("streamed", [False, True])
+def test_precision_form_unit_cube(streamed):
+    # streamed: the 16-warp kernel on the tiny coarse system (one ragged
+    # slice, every other warp idle; residual replacements included)
     sc = scenes.unit_cube(seed=1001)
-    rc, got = _mixed(sc, 1e-8)
+    rc, got = _mixed(sc, 1e-8, streamed=streamed)
     assert rc == agipc.OK
     _check(sc, got, 1e-8)
     ref = oracle.coarsened_step(sc, tol=1e-12)
