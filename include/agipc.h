@@ -174,6 +174,8 @@ typedef struct {
  * convergence, so the host never waits inside the loop.  The iteration is
  * the Chronopoulos-Gear form of PCG (one fused reduction per iteration);
  * mathematically it is the same method as the textbook recurrence.
+ * opt->streamed picks the kernel layout (see agipc_pcg_options); both reach
+ * the same solution up to rounding order.
  */
 int agipc_pcg(agipc_ctx *ctx, int32_t max_rows, const int32_t *n_rows_dev, const int32_t *row_ptr,
               const int32_t *col, const double *val, const double *dinv, const double *b, double *x,

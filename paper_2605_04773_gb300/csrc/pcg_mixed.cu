@@ -9,10 +9,12 @@
 // on GB300 are ~56x faster than the FP64 ones.
 //
 // Same structure as the FP64 kernel (pcg.cu): one persistent cooperative
-// launch, Chronopoulos-Gear recurrence, FP32 slices of 128 blocks staged by
-// cp.async and resident in shared memory when they fit.  A refinement
-// iteration adds an FP64 slice SpMV of x (staged in the warp's free buffer)
-// and one grid barrier.
+// launch, Chronopoulos-Gear recurrence, FP32 slices of 128 blocks, in the
+// same two layouts: 8 warps per SM (slices resident in shared memory when
+// they fit, else streamed through a ring of three) or 16 warps per SM (a
+// ring of two, always streamed).  Streamed full slices arrive by TMA bulk
+// copy on per-slot mbarriers.  A refinement iteration adds an FP64 slice
+// SpMV of x (staged in the warp's free buffer space) and one grid barrier.
 #include <algorithm>
 
 #include "agipc_common.cuh"
