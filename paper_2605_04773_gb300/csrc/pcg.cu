@@ -282,8 +282,9 @@ __global__ void __launch_bounds__(32 * kW, 1) pcg_kernel(PcgArgs A)
     // holds each buffer's next parity, `pend` the buffers with a bulk copy in
     // flight (drained before the kernel ends).  A resident slice is loaded
     // once by cp.async.  The 16-warp layout keeps cp.async for every slice:
-    // at its 128 registers the bulk path's state spilled and measured slower
-    // (100.3 against 98.2 us per iteration on the 2.28M-block fine system).
+    // at its 128 registers the bulk path's state spills, and it measured
+    // slower (100.3 against 96.1 us per iteration on the 2.28M-block fine
+    // system).
     constexpr bool kBulk = !kWide;
     uint64_t *mbar = s_mbar + 2 * wib;
     unsigned ph = 0, pend = 0;
@@ -339,7 +340,7 @@ __global__ void __launch_bounds__(32 * kW, 1) pcg_kernel(PcgArgs A)
                 if (sl != gwarp) slice_issue(0, sl);
                 slice_wait(0, sl);
                 const int cnt = (int)min64(kSlice, nnz - sl * kSlice);
-                slice_spmv<double, true>(wbuf, cnt, u, w, rowflag, join, lane, dpart);
+                slice_spmv<double, true, true>(wbuf, cnt, u, w, rowflag, join, lane, dpart);
             }
         } else {
             for (int64_t sl = gwarp; sl < nslices; sl += nwarps) {

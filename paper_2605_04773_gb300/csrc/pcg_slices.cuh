@@ -293,17 +293,22 @@ __device__ __forceinline__ void load_chunk(const double *src, double (&v)[18])
 // are written only in other phases, each followed by a grid barrier whose
 // acquire orders those writes before these loads (PTX memory model), so no
 // L1 line read here can predate them.
-template <class T>
+//
+// kLazy keeps u of the segment rows only for the lane's first block (which
+// always starts a segment); slice_compute loads it for later segment starts
+// when it meets them.  That saves 9 registers of T per lane, which the
+// 16-warp FP64 kernel (at most 128 registers) would otherwise spill.
+template <class T, bool kLazy = false>
 struct SliceGather {
     int rows_[kK];
     T xv[kK][3];
-    T ur[kK][3];
+    T ur[kLazy ? 1 : kK][3];
     int flags[kK];
 };
 
-template <class T>
+template <class T, bool kLazy = false>
 __device__ __forceinline__ void slice_gather(const unsigned char *buf, int cnt, const T *u, const uint8_t *rowflag,
-                                             int lane, SliceGather<T> &G)
+                                             int lane, SliceGather<T, kLazy> &G)
 {
     const int32_t *s_col = reinterpret_cast<const int32_t *>(buf + SliceLayout<T>::kVal);
     const int32_t *s_row = reinterpret_cast<const int32_t *>(buf + SliceLayout<T>::kVal + kIdxBytes);
@@ -313,7 +318,7 @@ __device__ __forceinline__ void slice_gather(const unsigned char *buf, int cnt, 
         G.rows_[j] = -1;
         G.flags[j] = 0;
         G.xv[j][0] = G.xv[j][1] = G.xv[j][2] = T(0);
-        G.ur[j][0] = G.ur[j][1] = G.ur[j][2] = T(0);
+        if (!kLazy || j == 0) G.ur[kLazy ? 0 : j][0] = G.ur[kLazy ? 0 : j][1] = G.ur[kLazy ? 0 : j][2] = T(0);
         if (q < cnt) {
             const int rj = s_row[q];
             G.rows_[j] = rj;
@@ -322,10 +327,12 @@ __device__ __forceinline__ void slice_gather(const unsigned char *buf, int cnt, 
             G.xv[j][1] = uc[1];
             G.xv[j][2] = uc[2];
             if (j == 0 || rj != s_row[q - 1]) {  // first block of a row segment
-                const T *up = u + 3 * (int64_t)rj;
-                G.ur[j][0] = up[0];
-                G.ur[j][1] = up[1];
-                G.ur[j][2] = up[2];
+                if (!kLazy || j == 0) {
+                    const T *up = u + 3 * (int64_t)rj;
+                    G.ur[kLazy ? 0 : j][0] = up[0];
+                    G.ur[kLazy ? 0 : j][1] = up[1];
+                    G.ur[kLazy ? 0 : j][2] = up[2];
+                }
                 G.flags[j] = rowflag[rj];
             }
         }
@@ -380,14 +387,13 @@ __device__ __forceinline__ void slice_gather_packed(const unsigned char *buf, in
 // inside the lane where they are stored.  Segments that cross lanes are
 // joined by the lane where the row starts, which walks forward over the
 // lanes that continue it.
-template <class T, bool kDelta>
-__device__ __forceinline__ void slice_compute(const unsigned char *buf, const SliceGather<T> &G, T *w,
-                                              unsigned char *join, int lane, double &dpart)
+template <class T, bool kDelta, bool kLazy = false>
+__device__ __forceinline__ void slice_compute(const unsigned char *buf, const SliceGather<T, kLazy> &G, T *w,
+                                              unsigned char *join, int lane, double &dpart, const T *u = nullptr)
 {
     const T *s_val = reinterpret_cast<const T *>(buf);
     const int(&rows_)[kK] = G.rows_;
     const T(&xv)[kK][3] = G.xv;
-    const T(&ur)[kK][3] = G.ur;
     bool split[kK];
 #pragma unroll
     for (int j = 0; j < kK; ++j) split[j] = (G.flags[j] & 1) != 0;
@@ -413,9 +419,16 @@ __device__ __forceinline__ void slice_compute(const unsigned char *buf, const Sl
         T B[9];
 #pragma unroll
         for (int e = 0; e < 9; ++e) B[e] = dsel(valid, ch[9 * (j % kBpc) + e], T(0));
+        if (kDelta && kLazy && j > 0 && start) {   // a later segment start: u of its row now
+            const T *up = u + 3 * (int64_t)rows_[j];
+            cu[0] = up[0];
+            cu[1] = up[1];
+            cu[2] = up[2];
+        }
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            cu[c] = dsel(start, ur[j][c], cu[c]);
+            if (!kLazy) cu[c] = dsel(start, G.ur[j][c], cu[c]);
+            else if (j == 0) cu[c] = dsel(start, G.ur[0][c], cu[c]);
             acc[c] = dsel(start, T(0), acc[c]);
             acc[c] = fma(B[3 * c + 2], xv[j][2], fma(B[3 * c + 1], xv[j][1], fma(B[3 * c], xv[j][0], acc[c])));
         }
@@ -447,13 +460,13 @@ __device__ __forceinline__ void slice_compute(const unsigned char *buf, const Sl
 }
 
 // Gather, then multiply: one slice with nothing overlapped.
-template <class T, bool kDelta>
+template <class T, bool kDelta, bool kLazy = false>
 __device__ __forceinline__ void slice_spmv(const unsigned char *buf, int cnt, const T *u, T *w,
                                            const uint8_t *rowflag, unsigned char *join, int lane, double &dpart)
 {
-    SliceGather<T> G;
-    slice_gather<T>(buf, cnt, u, rowflag, lane, G);
-    slice_compute<T, kDelta>(buf, G, w, join, lane, dpart);
+    SliceGather<T, kLazy> G;
+    slice_gather<T, kLazy>(buf, cnt, u, rowflag, lane, G);
+    slice_compute<T, kDelta, kLazy>(buf, G, w, join, lane, dpart, u);
 }
 
 }  // namespace pcgs
