@@ -1,7 +1,9 @@
 // Slice machinery shared by the persistent PCG kernels: constants of the
-// warp slices, cp.async staging, CTA sums, and the slice SpMV w = A u over
-// 128 consecutive 3x3 blocks (32 lanes x 4 blocks), templated on the type of
-// the matrix values, the vectors and the accumulation.
+// warp slices, slice staging (cp.async, and TMA bulk copies completing on
+// mbarriers), CTA sums, and the slice SpMV w = A u over 128 consecutive 3x3
+// blocks (32 lanes x 4 blocks) in two steps (gather, then multiply),
+// templated on the type of the matrix values, the vectors and the
+// accumulation.
 #pragma once
 
 #include "agipc_common.cuh"
