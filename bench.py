@@ -134,19 +134,32 @@ class ClockSampler:
                 "samples": len(sms), "reasons": sorted(reasons)}
 
 
+TRAFFIC_SOURCES = ("paper_2605_04773_gb300/csrc/pcg.cu", "paper_2605_04773_gb300/csrc/agipc_common.cuh",
+                   "paper_2605_04773_gb300/csrc/pcg_slices.cuh")
+
+
+def kernel_source_hash(files=TRAFFIC_SOURCES) -> str:
+    """sha256 of the kernel sources with comments and whitespace removed, so
+    that only a change of the code itself invalidates a stored capture."""
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    for f in files:
+        text = open(os.path.join(ROOT, f)).read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
+    return h.hexdigest()
+
+
 def _traffic_record():
     """DRAM bytes per launch of pcg_kernel from the committed ncu capture,
-    only while the kernel's source is the one that was captured."""
-    import hashlib
+    only while the kernel's code is the one that was captured."""
     path = os.path.join(ROOT, "profiles", "pcg_kernel_domino_8x8_coarse.json")
     if not os.path.exists(path):
         return None
     rec = json.load(open(path))
-    h = hashlib.sha256()
-    for f in ("paper_2605_04773_gb300/csrc/pcg.cu", "paper_2605_04773_gb300/csrc/agipc_common.cuh",
-              "paper_2605_04773_gb300/csrc/pcg_slices.cuh"):
-        h.update(open(os.path.join(ROOT, f), "rb").read())
-    if h.hexdigest() != rec.get("source_sha256"):
+    if kernel_source_hash() != rec.get("source_sha256"):
         return None
     return rec["dram_bytes_read"] + rec["dram_bytes_write"]
 
