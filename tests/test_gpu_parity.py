@@ -285,6 +285,18 @@ def test_status_not_converged_and_zero_rhs(streamed):
     ctx.close()
 
 
+def test_assembly_run_accepts_only_its_lengths():
+    sc = scenes.unit_cube(seed=1001)
+    ds = agipc.DeviceScene(sc)
+    ctx = ds.context()
+    for bad in (0, 2, 7, 64, -8):
+        with pytest.raises(agipc.AgipcError):
+            ctx.set_assembly_run(bad)
+    for good in (4, 8, 16, 32):
+        ctx.set_assembly_run(good)
+    ctx.close()
+
+
 def test_status_bad_index_and_capacity():
     sc = scenes.unit_cube(seed=1001)
     ds = agipc.DeviceScene(sc)
